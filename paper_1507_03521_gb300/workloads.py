@@ -1,0 +1,182 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests, the oracle's tests
+and the benchmark.
+
+This module holds no arithmetic of the scheme itself: only parameter sets
+(plain dicts in the paper's notation) and initial order-parameter fields
+(tanh-profiled droplets and layers, the initial conditions of Secs. 4.1-4.2).
+Random draws use NumPy's PCG64 with explicit seeds.
+
+Field layout: numpy arrays of shape [ny, nx], x fastest; node (i, j) sits at
+x = i, y = j.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+PERIODIC = 0
+WALL = 1
+
+
+def _base(**kw) -> dict:
+    d = dict(nx=64, ny=64, rho_A=1.0, rho_B=0.1, phi_A=1.0, phi_B=-1.0, sigma=0.01, W=4.0,
+             M=0.1, tau_f=0.8, tau_g=0.8, gravity=0.0, rho_ref=1.0, bc_x=PERIODIC,
+             bc_y=PERIODIC, u_wall_bottom=0.0, u_wall_top=0.0)
+    d.update(kw)
+    return d
+
+
+# --------------------------------------------------------------- fields
+
+def droplet_field(nx, ny, xc, yc, R, W, phi_A, phi_B, periodic=True):
+    """phi = mean + (dphi/2) tanh(2 (R - r)/W) around (xc, yc), r measured to
+    the nearest periodic image when periodic (initial condition of Sec. 4.2)."""
+    x = np.arange(nx, dtype=np.float64)[None, :]
+    y = np.arange(ny, dtype=np.float64)[:, None]
+    dx = np.abs(x - xc)
+    dy = np.abs(y - yc)
+    if periodic:
+        dx = np.minimum(dx, nx - dx)
+        dy = np.minimum(dy, ny - dy)
+    r = np.sqrt(dx * dx + dy * dy)
+    return 0.5 * (phi_A + phi_B) + 0.5 * (phi_A - phi_B) * np.tanh(2.0 * (R - r) / W)
+
+
+def layer_field(nx, ny, y_lo, y_hi, W, phi_A, phi_B):
+    """Fluid A in y_lo <= y <= y_hi between two tanh interfaces (Sec. 4.1)."""
+    y = np.arange(ny, dtype=np.float64)[:, None] * np.ones((1, nx))
+    mid = 0.5 * (y_lo + y_hi)
+    a = np.where(y <= mid, np.tanh(2.0 * (y - y_lo) / W), -np.tanh(2.0 * (y - y_hi) / W))
+    return 0.5 * (phi_A + phi_B) + 0.5 * (phi_A - phi_B) * a
+
+
+def multi_droplet_field(nx, ny, centres, radii, W, phi_A, phi_B):
+    """phi = max over droplets of the tanh profile, background phi_B
+    (periodic nearest-image distance).  Each droplet only touches a box of
+    half-width R + 6W around its centre, where the profile differs from
+    phi_B by more than 1e-10 relative."""
+    mean, half = 0.5 * (phi_A + phi_B), 0.5 * (phi_A - phi_B)
+    phi = np.full((ny, nx), float(phi_B))
+    for (xc, yc), R in zip(centres, radii):
+        h = int(math.ceil(R + 6 * W))
+        xs = np.arange(int(math.floor(xc)) - h, int(math.floor(xc)) + h + 2)
+        ys = np.arange(int(math.floor(yc)) - h, int(math.floor(yc)) + h + 2)
+        dx = (xs - xc)[None, :]
+        dy = (ys - yc)[:, None]
+        r = np.sqrt(dx * dx + dy * dy)
+        v = mean + half * np.tanh(2.0 * (R - r) / W)
+        xi = np.mod(xs, nx)
+        yi = np.mod(ys, ny)
+        sub = phi[np.ix_(yi, xi)]
+        phi[np.ix_(yi, xi)] = np.maximum(sub, v)
+    return phi
+
+
+def seeded_droplets(nx, ny, n, rmin, rmax, W, seed, max_tries=200000):
+    """n non-overlapping droplets: centres uniform, radii uniform in
+    [rmin, rmax], rejection-sampled so that centre distances (nearest
+    periodic image) are at least R1 + R2 + 2W."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    centres, radii = [], []
+    tries = 0
+    while len(centres) < n:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("could not place droplets")
+        R = rng.uniform(rmin, rmax)
+        c = (rng.uniform(0, nx), rng.uniform(0, ny))
+        ok = True
+        for (x2, y2), R2 in zip(centres, radii):
+            dx = abs(c[0] - x2)
+            dy = abs(c[1] - y2)
+            dx = min(dx, nx - dx)
+            dy = min(dy, ny - dy)
+            if dx * dx + dy * dy < (R + R2 + 2 * W) ** 2:
+                ok = False
+                break
+        if ok:
+            centres.append(c)
+            radii.append(R)
+    return centres, radii
+
+
+def rt_field(nx, ny, W, phi_A, phi_B, y0, amp):
+    """Heavy fluid A above y_i(x) = y0 + amp cos(2 pi x / nx)."""
+    x = np.arange(nx, dtype=np.float64)[None, :]
+    y = np.arange(ny, dtype=np.float64)[:, None]
+    yi = y0 + amp * np.cos(2.0 * np.pi * x / nx)
+    return 0.5 * (phi_A + phi_B) + 0.5 * (phi_A - phi_B) * np.tanh(2.0 * (y - yi) / W)
+
+
+# ------------------------------------------------------------ workloads
+
+def droplet64():
+    """Stationary droplet, 64x64 periodic, phi in [-1, 1], R = 16, W = 4,
+    rho_A = 1, rho_B = 0.1, sigma = 0.01, M = 0.1, tau_f = tau_g = 0.8."""
+    p = _base(nx=64, ny=64)
+    phi = droplet_field(64, 64, 32.0, 32.0, 16.0, 4.0, 1.0, -1.0)
+    return p, phi
+
+
+def rayleigh_taylor(nx=256, ny=1024):
+    """Rayleigh-Taylor, heavy over light, rho_A/rho_B = 3, W = 4,
+    sigma = 5e-5, sqrt(g L) = 0.04, Re = 3000 with L = nx, periodic in x,
+    no-slip walls at y = -1/2 and y = ny - 1/2.  g = 0.04^2/L,
+    nu = 0.04 L / 3000 -> tau_f = 0.5 + 3 nu; tau_g = 0.8;
+    M = 0.04 L / 1000; rho_ref = (rho_A + rho_B)/2."""
+    L = float(nx)
+    g = 0.04 ** 2 / L
+    nu = 0.04 * L / 3000.0
+    p = _base(nx=nx, ny=ny, rho_A=1.0, rho_B=1.0 / 3.0, sigma=5e-5, W=4.0,
+              M=0.04 * L / 1000.0, tau_f=0.5 + 3.0 * nu, tau_g=0.8, gravity=g,
+              rho_ref=0.5 * (1.0 + 1.0 / 3.0), bc_y=WALL)
+    phi = rt_field(nx, ny, 4.0, 1.0, -1.0, ny / 2.0, 0.1 * nx)
+    return p, phi
+
+
+def precision(n=4096, n_drops=512, seed=1507035):
+    """n x n periodic, n_drops droplets of radius U[8, 40] (fluid A inside),
+    W = 4, rho_A = 1, rho_B = 0.01, sigma = 1e-3, M = 0.05, tau = 0.8."""
+    p = _base(nx=n, ny=n, rho_A=1.0, rho_B=0.01, sigma=1e-3, M=0.05)
+    centres, radii = seeded_droplets(n, n, n_drops, 8.0, 40.0, 4.0, seed)
+    phi = multi_droplet_field(n, n, centres, radii, 4.0, 1.0, -1.0)
+    return p, phi
+
+
+def paper_droplet(R=25.0, n=100, Pe=50.0, Cn=4.0):
+    """Stationary droplet of Sec. 4.2: 100x100 periodic, rho_A = 1,
+    rho_B = 0.2, tau_f = tau_g = 1, phi_A = 1, phi_B = 0, sigma = 1e-3,
+    W = Cn, lambda = 1/(Pe beta) with beta = 12 sigma / W (U_c = L_c = 1)."""
+    sigma, W = 1e-3, float(Cn)
+    beta = 12.0 * sigma / W
+    p = _base(nx=n, ny=n, rho_A=1.0, rho_B=0.2, phi_A=1.0, phi_B=0.0, sigma=sigma, W=W,
+              M=1.0 / (Pe * beta), tau_f=1.0, tau_g=1.0, rho_ref=1.0)
+    phi = droplet_field(n, n, n / 2.0, n / 2.0, R, W, 1.0, 0.0)
+    return p, phi
+
+
+def paper_flat(nx=10, ny=100, Pe=50.0, Cn=4.0):
+    """Flat interface of Sec. 4.1: fluid A in 25 <= y <= 75, periodic."""
+    sigma, W = 1e-3, float(Cn)
+    beta = 12.0 * sigma / W
+    p = _base(nx=nx, ny=ny, rho_A=1.0, rho_B=0.2, phi_A=1.0, phi_B=0.0, sigma=sigma, W=W,
+              M=1.0 / (Pe * beta), tau_f=1.0, tau_g=1.0, rho_ref=1.0)
+    phi = layer_field(nx, ny, 25.0, 75.0, W, 1.0, 0.0)
+    return p, phi
+
+
+def small_case(nx, ny, seed, walls=False, gravity=0.0, u_wall=0.0, rho_ratio=10.0):
+    """A small seeded domain for parity: an off-centre droplet with a
+    seeded velocity perturbation, phi in [-1, 1]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    R = 0.3 * min(nx, ny)
+    xc = nx / 2.0 + rng.uniform(-1, 1)
+    yc = ny / 2.0 + rng.uniform(-1, 1)
+    p = _base(nx=nx, ny=ny, rho_A=1.0, rho_B=1.0 / rho_ratio, sigma=0.01, W=4.0, M=0.1,
+              tau_f=0.8, tau_g=0.9, gravity=gravity, rho_ref=0.5 * (1.0 + 1.0 / rho_ratio),
+              bc_y=WALL if walls else PERIODIC, u_wall_bottom=-u_wall, u_wall_top=u_wall)
+    phi = droplet_field(nx, ny, xc, yc, R, 4.0, 1.0, -1.0, periodic=not walls)
+    ux = 0.01 * rng.standard_normal((ny, nx))
+    uy = 0.01 * rng.standard_normal((ny, nx))
+    return p, phi, ux, uy
