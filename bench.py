@@ -1,0 +1,349 @@
+"""Throughput benchmark of the time step on GB300.
+
+Workload: the precision configuration, 4096 x 4096 periodic, 512 seeded
+droplets (radii uniform in [8, 40], W = 4, rho_A/rho_B = 100, sigma = 1e-3,
+M = 0.05, tau_f = tau_g = 0.8).  A "step" is one full time step of both
+populations over the whole grid (one kernel launch).  MLUPS = cells x
+steps / seconds.
+
+Our arm (default): FP32 form timed with CUDA events on the simulation's
+stream; the populations (2.4 GB per time level) exceed L2, so no flush is
+needed between steps.  Also reported: the 16-bit storage forms and the FP64
+form with their errors against the FP64 path, the roofline of the step
+kernel, an end-to-end number through the C ABI with host buffers, and the
+FP64 CPU oracle on a bounded sample (cpu_baseline).
+
+--impl reference: the reference arm is the FP64 CPU oracle timed on the
+host cores on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): each rank advances its own replica of the domain
+(weak scaling, no collective on the data path); the step time is the
+maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_CELL = {"f64": 288, "f32": 144, "f16s": 76, "bf16s": 76}
+WORKLOAD = "precision-4096x4096-512-droplets-rho100"
+CPU_SAMPLE_N, CPU_SAMPLE_DROPS, CPU_SAMPLE_STEPS = 1024, 32, 20
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1507_03521_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(dtype: str):
+    """DRAM bytes per launch of the step kernel from a committed ncu
+    summary, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(dtype)
+        if e and e.get("kernel_hash") == _kernel_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def time_steps(sim, steps, warmup):
+    """Per-launch CUDA-event timing of `steps` steps on the sim's stream."""
+    import torch
+    sim.step(warmup)
+    st = sim.stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(st)
+    for i in range(steps):
+        sim.step(1)
+        ev[i + 1].record(st)
+    torch.cuda.synchronize()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    return ev[0].elapsed_time(ev[-1]), per
+
+
+def cpu_baseline():
+    """FP64 oracle, single thread, on a bounded sample of the workload:
+    1024 x 1024 with 32 droplets (the workload's droplet density and
+    parameters), 20 steps."""
+    import oracle
+    from paper_1507_03521_gb300 import workloads as W
+    p, phi = W.precision(n=CPU_SAMPLE_N, n_drops=CPU_SAMPLE_DROPS, seed=1507035)
+    o = oracle.Oracle(p)
+    o.init_phi(phi)
+    t0 = time.perf_counter()
+    o.step(CPU_SAMPLE_STEPS)
+    dt = time.perf_counter() - t0
+    mlups = CPU_SAMPLE_N * CPU_SAMPLE_N * CPU_SAMPLE_STEPS / dt / 1e6
+    return {"value": round(mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{CPU_SAMPLE_N}x{CPU_SAMPLE_N}, {CPU_SAMPLE_DROPS} droplets, same parameters, "
+                      f"{CPU_SAMPLE_STEPS} steps, {dt:.1f} s, FP64 single thread"}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle as it stands, one oracle step per
+    benchmark step, on a 512 x 512 sample of the workload (8 droplets: the
+    workload's droplet density, same parameters)."""
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1507_03521_gb300 import workloads as W
+    n, nd = 512, 8
+    p, phi = W.precision(n=n, n_drops=nd, seed=1507035)
+    o = oracle.Oracle(p)
+    o.init_phi(phi)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = round(n * n * args.steps / dt / 1e6, 4)
+    sample = f"{n}x{n}, {nd} droplets, same parameters, FP64 single thread, {args.steps} steps"
+    line = {"impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / max(args.steps, 1) * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=4096, help="grid side (default: the workload's)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the f16s/bf16s/f64 forms")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1507_03521_gb300 import build, lbm, workloads as W
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    n = args.n
+    n_drops = 512 if n == 4096 else max(1, int(512 * (n / 4096) ** 2))
+    p, phi = W.precision(n=n, n_drops=n_drops)
+    cells = n * n
+    peak, peak_kind = _peaks()
+
+    def measure(dtype, steps, warmup, clocks=False):
+        sim = lbm.Sim(p, dtype)
+        sim.init_phi(phi)
+        if dist is not None:
+            torch.cuda.synchronize()
+            dist.barrier()
+        if clocks:
+            with Clocks(torch.cuda.current_device()) as ck:
+                total, per = time_steps(sim, steps, warmup)
+            ckinfo = ck.summary()
+        else:
+            total, per = time_steps(sim, steps, warmup)
+            ckinfo = None
+        if dist is not None:
+            t = torch.tensor([total], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+            torch.cuda.synchronize()
+            dist.barrier()
+        return sim, total, per, ckinfo
+
+    sim, total_ms, per, ck = measure("f32", args.steps, args.warmup, clocks=True)
+    ms = total_ms / args.steps
+    mlups = cells * args.steps * world / (total_ms * 1e-3) / 1e6
+    avg_launch_ms = statistics.mean(per)
+    alg = BYTES_PER_CELL["f32"] * cells
+    achieved = alg / (avg_launch_ms * 1e-3) / 1e9
+    sim.close()
+
+    line = {"metric": "MLUPS", "value": round(mlups, 2), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": n, "ny": n, "droplets": n_drops,
+                       "rho_ratio": 100, "storage": "f32", "parallelism": f"replicas{world}",
+                       "l2": "no flush: populations 2.4 GB per time level > 129 MB L2"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": _traffic("f32"), "peak_kind": peak_kind,
+                         "bytes_per_cell": BYTES_PER_CELL["f32"], "kernel": "k_step<float>"},
+            "gpu_launches": args.steps, "clocks": ck}
+
+    if not args.no_forms:
+        forms = {}
+        ref = None
+        for dtype in ("f64", "f16s", "bf16s"):
+            ksteps = args.steps if dtype != "f64" else max(10, args.steps // 10)
+            s2, tot, per2, _ = measure(dtype, ksteps, args.warmup)
+            m2 = cells * ksteps * world / (tot * 1e-3) / 1e6
+            ach2 = BYTES_PER_CELL[dtype] * cells / (statistics.mean(per2) * 1e-3) / 1e9
+            forms[dtype] = {"mlups": round(m2, 2), "ms_per_step": round(tot / ksteps, 5),
+                            "hbm_gbs": round(ach2, 1), "frac": round(ach2 / peak, 4),
+                            "bytes_per_cell": BYTES_PER_CELL[dtype]}
+            s2.close()
+        # errors after the same number of steps, against the FP64 path
+        errs = {}
+        K = args.warmup + args.steps
+        s64 = lbm.Sim(p, "f64")
+        s64.init_phi(phi)
+        s64.step(K)
+        ref = s64.fields(("phi", "ux", "uy"))
+        s64.close()
+        for dtype in ("f32", "f16s", "bf16s"):
+            s3 = lbm.Sim(p, dtype)
+            s3.init_phi(phi)
+            s3.step(K)
+            f3 = s3.fields(("phi", "ux", "uy"))
+            s3.close()
+            errs[dtype] = {k: float((f3[k].double() - ref[k]).abs().max().item()) for k in f3}
+        for dtype in ("f16s", "bf16s"):
+            forms[dtype]["gain_vs_f32"] = round(forms[dtype]["mlups"] / mlups, 3)
+            forms[dtype]["max_abs_err_vs_f64"] = errs[dtype]
+            forms[dtype]["steps_for_err"] = K
+        forms["f32"] = {"max_abs_err_vs_f64": errs["f32"], "steps_for_err": K}
+        line["forms"] = forms
+
+    # End to end through the C ABI with host buffers: phi0 in, K steps,
+    # phi/u/p out and the mass diagnostic, all inside the timed region.
+    npdt = np.float32
+    phi_h = torch.from_numpy(phi.astype(npdt)).pin_memory().numpy()
+    outs = {k: torch.empty((n, n), dtype=torch.float32).pin_memory().numpy()
+            for k in ("phi", "ux", "uy", "p")}
+    sim = lbm.Sim(p, "f32")
+    sim.init_phi_host(phi_h)
+    sim.step(args.warmup)
+    sim.fields_host(out=outs)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    sim.init_phi_host(phi_h)
+    sim.step(args.steps)
+    sim.fields_host(out=outs)
+    sim.mass()
+    t_e2e = time.perf_counter() - t0
+    sim.close()
+    if dist is not None:
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    h2d = phi_h.nbytes
+    d2h = sum(v.nbytes for v in outs.values()) + 16
+    line["e2e"] = {"value": round(cells * args.steps * world / t_e2e / 1e6, 2), "unit": "MLUPS",
+                   "h2d_bytes_per_step": round(h2d / args.steps, 1),
+                   "d2h_bytes_per_step": round(d2h / args.steps, 1),
+                   "note": "one C-ABI job: phi0 from pinned host memory, init, steps, "
+                           "4 fields + mass back to host; bytes are per step of the job"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

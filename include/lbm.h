@@ -1,0 +1,177 @@
+/*
+ * lbm.h — C ABI of the GB300 (sm_103a) quasi-incompressible phase-field
+ * lattice Boltzmann solver of Yang & Guo (arXiv 1507.03521), D2Q9.
+ *
+ * The method: two coupled lattice Boltzmann equations advanced together
+ * each time step (Sec. 3):
+ *   - f_i, the FLOW population (Eq. 22), relaxed with tau_f (viscosity
+ *     nu = cs2 (tau_f - 1/2), Eq. 33), whose moments give the pressure p
+ *     (Eq. 32) and the velocity u (Eq. 31);
+ *   - g_i, the PHASE-FIELD population (Eq. 23), relaxed with tau_g
+ *     (mobility lambda = cs2 (tau_g - 1/2) alpha, Eq. 33), whose zeroth
+ *     moment is the order parameter phi (Eq. 30).
+ * Naming follows the paper: f is flow, g is phase.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns lbm_status; LBM_OK is 0, errors are negative.
+ *     After an error, lbm_last_error(sim) holds a one-line message.
+ *   - Fields are row-major [ny][nx], x fastest; y is the wall and gravity
+ *     direction.  The field element type is double for LBM_F64 and float
+ *     for every other dtype ("field type" below).
+ *   - Device work is asynchronous on the stream given to lbm_create (a
+ *     cudaStream_t, NULL for the legacy default stream).  Calls that hand
+ *     results to the host (lbm_mass, lbm_laplace, and any *_host variant)
+ *     synchronise that stream.  Asynchronous CUDA errors surface at the
+ *     next synchronising call as LBM_ERR_CUDA.
+ *   - The library allocates no device memory of its own for a simulation:
+ *     the caller allocates the two buffers sized by lbm_buffer_sizes and
+ *     binds them with lbm_bind_buffers.  They must stay valid until
+ *     lbm_destroy; the library never frees them.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_sim lbm_sim; /* opaque handle, owned by the caller */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,       /* invalid argument or parameter set */
+    LBM_ERR_CUDA = -2,      /* a CUDA runtime call failed */
+    LBM_ERR_NONFINITE = -3, /* a reduction met NaN or Inf in the state */
+    LBM_ERR_TIMEOUT = -4,   /* reserved: a bounded device wait ran out */
+    LBM_ERR_STATE = -5,     /* call out of order (e.g. step before init) */
+    LBM_ERR_NOMEM = -6      /* a bound buffer is too small */
+} lbm_status;
+
+typedef enum {
+    LBM_F64 = 0,  /* populations and arithmetic in FP64 */
+    LBM_F32 = 1,  /* populations and arithmetic in FP32 */
+    LBM_F16S = 2, /* FP32 arithmetic; f_0..8 and g_1..8 stored as scaled FP16, g_0 in FP32 */
+    LBM_BF16S = 3 /* FP32 arithmetic; f_0..8 and g_1..8 stored as BF16, g_0 in FP32 */
+} lbm_dtype;
+
+typedef enum { LBM_PERIODIC = 0, LBM_WALL = 1 } lbm_bc;
+
+/* Physical and lattice parameters of one domain, in lattice units
+ * (dx = dt = 1, D2Q9, cs2 = 1/3; Sec. 3).
+ *   nx, ny          grid size, each >= 5
+ *   rho_A, rho_B    densities of fluids A and B (> 0)
+ *   phi_A, phi_B    bulk order parameters of A and B (distinct)
+ *   sigma, W        surface tension and interface width; they fix
+ *                   kappa = 3 sigma W / (2 dphi^2) and
+ *                   beta = 12 sigma / (W dphi^4), dphi = phi_A - phi_B
+ *                   (Eqs. 3-4 solved for kappa and beta)
+ *   M               mobility lambda of the Cahn-Hilliard equation (Eq. 7)
+ *   tau_f, tau_g    relaxation times of f (flow) and g (phase), > 1/2
+ *   gravity, rho_ref body force F_b = (0, -(rho - rho_ref) gravity)
+ *                   (the form of Sec. 4.3 with rho_A replaced by rho_ref)
+ *   bc_x            LBM_PERIODIC only
+ *   bc_y            LBM_PERIODIC, or LBM_WALL: no-slip walls at y = -1/2
+ *                   and y = ny - 1/2 (halfway bounce-back)
+ *   u_wall_bottom, u_wall_top  x-velocity of the walls (LBM_WALL only)
+ *   dtype           an lbm_dtype */
+typedef struct {
+    int nx, ny;
+    double rho_A, rho_B, phi_A, phi_B;
+    double sigma, W, M, tau_f, tau_g;
+    double gravity, rho_ref;
+    int bc_x, bc_y;
+    double u_wall_bottom, u_wall_top;
+    int dtype;
+} lbm_params;
+
+/* Library ABI version (this header: 1). */
+LBM_API int lbm_version(void);
+
+/* Bytes the caller must allocate on the device for one domain:
+ * *state_bytes for the populations (two time levels, ping-pong) and
+ * *work_bytes for field staging and reduction partials.  Both are
+ * multiples of 256.  Returns LBM_ERR_ARG for an invalid parameter set. */
+LBM_API lbm_status lbm_buffer_sizes(const lbm_params *prm, size_t *state_bytes, size_t *work_bytes);
+
+/* Validate prm and create a handle bound to `stream` (a cudaStream_t) on
+ * the current CUDA device.  Host memory only.  *out is NULL on error. */
+LBM_API lbm_status lbm_create(const lbm_params *prm, void *stream, lbm_sim **out);
+
+/* Bind caller-owned device buffers (>= the sizes of lbm_buffer_sizes,
+ * 256-byte aligned).  LBM_ERR_NOMEM if either is too small. */
+LBM_API lbm_status lbm_bind_buffers(lbm_sim *sim, void *state, size_t state_bytes, void *work,
+                            size_t work_bytes);
+
+/* Initial state (Secs. 4.1-4.2: "at equilibrium"): p = 0, u = (ux, uy)
+ * (zero where a pointer is NULL), mu from phi (Eq. 5), f = f^eq (Eq. 24),
+ * g = g^eq (Eq. 25).  phi, ux, uy: nx*ny elements of the field type, on
+ * the device (on_host = 0) or in host memory (on_host = 1, copied in on
+ * the stream, which is then synchronised).  Resets the step counter. */
+LBM_API lbm_status lbm_init_phi(lbm_sim *sim, const void *phi, const void *ux, const void *uy,
+                        int on_host);
+
+/* Advance n >= 0 time steps (Eqs. 22-23 with Eqs. 24-32, streaming,
+ * bounce-back).  Asynchronous; one kernel launch per step. */
+LBM_API lbm_status lbm_step(lbm_sim *sim, int64_t n);
+
+/* Macroscopic fields of the current time level: phi (Eq. 30), rho
+ * (Eq. 11), p (Eq. 32), ux and uy (Eq. 31), mu (Eq. 5).  Each output is
+ * nx*ny elements of the field type or NULL; device pointers for
+ * on_host = 0, host pointers for on_host = 1 (the stream is then
+ * synchronised before return). */
+LBM_API lbm_status lbm_fields(lbm_sim *sim, void *phi, void *rho, void *p, void *ux, void *uy, void *mu,
+                      int on_host);
+
+/* Total mass sum(rho) and total order parameter sum(phi) over the grid,
+ * accumulated in FP64 in a fixed order (bitwise reproducible).
+ * Synchronises the stream.  LBM_ERR_NONFINITE if either is NaN or Inf. */
+LBM_API lbm_status lbm_mass(lbm_sim *sim, double *mass, double *phi_total);
+
+/* Laplace-law diagnostic of Sec. 4.2 for a droplet centred at (xc, yc)
+ * with nominal radius R: *dP = mean total pressure
+ * P = p0 - kappa phi lap(phi) + kappa |grad phi|^2 / 2 + p, p0 = phi psi' - psi,
+ * over r < R - 2W minus its mean over r > R + 2W (nearest periodic image);
+ * *R_eff = sqrt(A / pi), A = sum (phi - phi_B) / (phi_A - phi_B).
+ * FP64 accumulation.  Synchronises the stream. */
+LBM_API lbm_status lbm_laplace(lbm_sim *sim, double xc, double yc, double R, double *dP, double *R_eff);
+
+/* Bytes of one time level of populations (what get/set_state copy). */
+LBM_API size_t lbm_state_bytes(const lbm_sim *sim);
+
+/* Copy the current populations out (dst) or in (src), device pointers for
+ * on_host = 0 and host pointers for on_host = 1.  The layout is the
+ * library's storage layout for the dtype; a state written by get_state
+ * and read back by set_state resumes bit-identically.  set_state also
+ * sets the step counter. */
+LBM_API lbm_status lbm_get_state(lbm_sim *sim, void *dst, int on_host, int64_t *step);
+LBM_API lbm_status lbm_set_state(lbm_sim *sim, const void *src, int on_host, int64_t step);
+
+/* Number of time steps taken since lbm_init_phi / lbm_set_state. */
+LBM_API int64_t lbm_step_count(const lbm_sim *sim);
+
+/* Last error message of this handle ("" if none).  Valid until the next
+ * call on the handle. */
+LBM_API const char *lbm_last_error(const lbm_sim *sim);
+
+/* Message of the last lbm_create / lbm_buffer_sizes failure in this
+ * thread (those calls have no handle to store it in). */
+LBM_API const char *lbm_create_error(void);
+
+/* Free the handle's host state.  Bound buffers stay the caller's. */
+LBM_API void lbm_destroy(lbm_sim *sim);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,335 @@
+// lbm_api.cu — the C ABI declared in include/lbm.h.
+//
+// Host-side bookkeeping only: parameter validation and derivation (Eqs. 3-4
+// solved for kappa and beta, Eq. 13, Eq. 17, Eq. 33), buffer layout, and
+// the launch sequence of each entry point.  Every step of the method runs
+// in the kernels of lbm_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+using lbm::Derived;
+using lbm::Ops;
+
+namespace {
+
+constexpr int kPartBlocks = 152 * 4;  // reduction grid: 4 CTAs per SM
+constexpr int kFieldSlots = 7;        // phi, rho, p, ux, uy, mu, P
+
+thread_local std::string g_create_err;
+
+size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+const Ops *ops_for(int dtype) {
+    switch (dtype) {
+        case LBM_F64: return lbm::ops_f64();
+        case LBM_F32: return lbm::ops_f32();
+        case LBM_F16S: return lbm::ops_f16s();
+        case LBM_BF16S: return lbm::ops_bf16s();
+        default: return nullptr;
+    }
+}
+
+// Parameter checks; returns an empty string when prm is valid.
+std::string check_params(const lbm_params *p) {
+    if (!p) return "null parameter block";
+    if (p->nx < 5 || p->ny < 5) return "nx and ny must be >= 5";
+    if ((long long)p->nx * p->ny > (1LL << 34)) return "grid too large";
+    if (!(p->tau_f > 0.5) || !(p->tau_g > 0.5)) return "tau_f and tau_g must exceed 1/2";
+    if (!(p->rho_A > 0.0) || !(p->rho_B > 0.0)) return "rho_A and rho_B must be positive";
+    if (!(p->W > 0.0)) return "W must be positive";
+    if (!(p->sigma >= 0.0) || !(p->M >= 0.0)) return "sigma and M must be non-negative";
+    if (!(p->phi_A != p->phi_B)) return "phi_A and phi_B must differ";
+    if (p->rho_B * p->phi_A - p->rho_A * p->phi_B == 0.0) return "gamma undefined for these rho, phi";
+    if (p->bc_x != LBM_PERIODIC) return "bc_x must be LBM_PERIODIC";
+    if (p->bc_y != LBM_PERIODIC && p->bc_y != LBM_WALL) return "bc_y must be LBM_PERIODIC or LBM_WALL";
+    if (!ops_for(p->dtype)) return "unknown dtype";
+    const double vals[] = {p->rho_A, p->rho_B, p->phi_A, p->phi_B, p->sigma, p->W, p->M,
+                           p->tau_f, p->tau_g, p->gravity, p->rho_ref, p->u_wall_bottom,
+                           p->u_wall_top};
+    for (double v : vals)
+        if (!std::isfinite(v)) return "non-finite parameter";
+    return "";
+}
+
+Derived derive(const lbm_params *p) {
+    Derived d;
+    d.nx = p->nx;
+    d.ny = p->ny;
+    d.wall = p->bc_y == LBM_WALL;
+    d.N = (long long)p->nx * p->ny;
+    d.NS = (d.N + 127) / 128 * 128;
+    const double dphi = p->phi_A - p->phi_B;
+    d.phiA = p->phi_A;
+    d.phiB = p->phi_B;
+    d.phibar = 0.5 * (p->phi_A + p->phi_B);
+    d.rhoB = p->rho_B;
+    d.drho = (p->rho_A - p->rho_B) / dphi;                    // Eq. 13
+    d.kappa = 3.0 * p->sigma * p->W / (2.0 * dphi * dphi);    // Eqs. 3-4
+    d.beta = 12.0 * p->sigma / (p->W * dphi * dphi * dphi * dphi);
+    d.lambda = p->M;
+    d.alpha = p->M / ((p->tau_g - 0.5) / 3.0);                // Eq. 33
+    d.gamma = (p->rho_A - p->rho_B) / (p->rho_B * p->phi_A - p->rho_A * p->phi_B);  // Eq. 17
+    d.grav = p->gravity;
+    d.rhoref = p->rho_ref;
+    d.tau_f = p->tau_f;
+    d.tau_g = p->tau_g;
+    d.uwb = d.wall ? p->u_wall_bottom : 0.0;
+    d.uwt = d.wall ? p->u_wall_top : 0.0;
+    return d;
+}
+
+struct Layout {
+    size_t level, state, field_slot, part_off, out_off, work;
+};
+
+Layout layout(const Derived &d, const Ops *ops) {
+    Layout L;
+    L.level = round256(ops->level_bytes(d.NS));
+    L.state = 2 * L.level;
+    L.field_slot = round256((size_t)d.NS * ops->field_size);
+    L.part_off = kFieldSlots * L.field_slot;
+    L.out_off = L.part_off + round256((size_t)kPartBlocks * 5 * sizeof(double));
+    L.work = L.out_off + 256;
+    return L;
+}
+
+}  // namespace
+
+struct lbm_sim {
+    lbm_params prm;
+    Derived d;
+    const Ops *ops;
+    Layout L;
+    cudaStream_t stream;
+    char *state = nullptr;
+    char *work = nullptr;
+    int cur = 0;  // index of the level holding the current time
+    int64_t steps = 0;
+    bool initialized = false;
+    std::string err;
+
+    char *level(int i) { return state + (size_t)i * L.level; }
+    char *slot(int i) { return work + (size_t)i * L.field_slot; }
+    double *part() { return reinterpret_cast<double *>(work + L.part_off); }
+    double *out() { return reinterpret_cast<double *>(work + L.out_off); }
+
+    lbm_status fail(lbm_status s, const std::string &m) {
+        err = m;
+        return s;
+    }
+    lbm_status cuda(cudaError_t e, const char *what) {
+        if (e == cudaSuccess) return LBM_OK;
+        err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+        return LBM_ERR_CUDA;
+    }
+    lbm_status ready() {
+        if (!state || !work) return fail(LBM_ERR_STATE, "buffers not bound");
+        return LBM_OK;
+    }
+};
+
+#define LBM_CK(sim, call)                                   \
+    do {                                                    \
+        lbm_status st__ = (sim)->cuda((call), #call);       \
+        if (st__ != LBM_OK) return st__;                    \
+    } while (0)
+
+extern "C" {
+
+int lbm_version(void) { return 1; }
+
+lbm_status lbm_buffer_sizes(const lbm_params *prm, size_t *state_bytes, size_t *work_bytes) {
+    std::string m = check_params(prm);
+    if (!m.empty()) {
+        g_create_err = m;
+        return LBM_ERR_ARG;
+    }
+    const Derived d = derive(prm);
+    const Layout L = layout(d, ops_for(prm->dtype));
+    if (state_bytes) *state_bytes = L.state;
+    if (work_bytes) *work_bytes = L.work;
+    return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_params *prm, void *stream, lbm_sim **out) {
+    if (!out) {
+        g_create_err = "null output pointer";
+        return LBM_ERR_ARG;
+    }
+    *out = nullptr;
+    std::string m = check_params(prm);
+    if (!m.empty()) {
+        g_create_err = m;
+        return LBM_ERR_ARG;
+    }
+    lbm_sim *s = new (std::nothrow) lbm_sim();
+    if (!s) {
+        g_create_err = "host allocation failed";
+        return LBM_ERR_NOMEM;
+    }
+    s->prm = *prm;
+    s->d = derive(prm);
+    s->ops = ops_for(prm->dtype);
+    s->L = layout(s->d, s->ops);
+    s->stream = static_cast<cudaStream_t>(stream);
+    g_create_err.clear();
+    *out = s;
+    return LBM_OK;
+}
+
+lbm_status lbm_bind_buffers(lbm_sim *s, void *state, size_t state_bytes, void *work,
+                            size_t work_bytes) {
+    if (!s) return LBM_ERR_ARG;
+    if (!state || !work) return s->fail(LBM_ERR_ARG, "null buffer");
+    if ((reinterpret_cast<uintptr_t>(state) & 255) || (reinterpret_cast<uintptr_t>(work) & 255))
+        return s->fail(LBM_ERR_ARG, "buffers must be 256-byte aligned");
+    if (state_bytes < s->L.state || work_bytes < s->L.work)
+        return s->fail(LBM_ERR_NOMEM, "bound buffer smaller than lbm_buffer_sizes");
+    s->state = static_cast<char *>(state);
+    s->work = static_cast<char *>(work);
+    s->initialized = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_init_phi(lbm_sim *s, const void *phi, const void *ux, const void *uy, int on_host) {
+    if (!s) return LBM_ERR_ARG;
+    if (lbm_status st = s->ready()) return st;
+    if (!phi) return s->fail(LBM_ERR_ARG, "phi is null");
+    const size_t fb = (size_t)s->d.N * s->ops->field_size;
+    const void *dphi = phi, *dux = ux, *duy = uy;
+    if (on_host) {
+        LBM_CK(s, cudaMemcpyAsync(s->slot(0), phi, fb, cudaMemcpyHostToDevice, s->stream));
+        dphi = s->slot(0);
+        if (ux) {
+            LBM_CK(s, cudaMemcpyAsync(s->slot(3), ux, fb, cudaMemcpyHostToDevice, s->stream));
+            dux = s->slot(3);
+        }
+        if (uy) {
+            LBM_CK(s, cudaMemcpyAsync(s->slot(4), uy, fb, cudaMemcpyHostToDevice, s->stream));
+            duy = s->slot(4);
+        }
+    }
+    s->cur = 0;
+    LBM_CK(s, s->ops->init(s->d, dphi, dux, duy, s->level(0), s->stream));
+    if (on_host) LBM_CK(s, cudaStreamSynchronize(s->stream));
+    s->steps = 0;
+    s->initialized = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_sim *s, int64_t n) {
+    if (!s) return LBM_ERR_ARG;
+    if (lbm_status st = s->ready()) return st;
+    if (!s->initialized) return s->fail(LBM_ERR_STATE, "lbm_step before lbm_init_phi");
+    if (n < 0) return s->fail(LBM_ERR_ARG, "negative step count");
+    for (int64_t t = 0; t < n; ++t) {
+        LBM_CK(s, s->ops->step(s->d, s->level(s->cur), s->level(1 - s->cur), s->stream));
+        s->cur = 1 - s->cur;
+        s->steps++;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_fields(lbm_sim *s, void *phi, void *rho, void *p, void *ux, void *uy, void *mu,
+                      int on_host) {
+    if (!s) return LBM_ERR_ARG;
+    if (lbm_status st = s->ready()) return st;
+    if (!s->initialized) return s->fail(LBM_ERR_STATE, "lbm_fields before lbm_init_phi");
+    void *user[6] = {phi, rho, p, ux, uy, mu};
+    void *dev[6];
+    for (int i = 0; i < 6; ++i) dev[i] = on_host ? (user[i] ? s->slot(i) : nullptr) : user[i];
+    LBM_CK(s, s->ops->fields(s->d, s->level(s->cur), dev[0], dev[1], dev[2], dev[3], dev[4],
+                             dev[5], nullptr, s->stream));
+    if (on_host) {
+        const size_t fb = (size_t)s->d.N * s->ops->field_size;
+        for (int i = 0; i < 6; ++i)
+            if (user[i])
+                LBM_CK(s, cudaMemcpyAsync(user[i], dev[i], fb, cudaMemcpyDeviceToHost, s->stream));
+        LBM_CK(s, cudaStreamSynchronize(s->stream));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_mass(lbm_sim *s, double *mass, double *phi_total) {
+    if (!s) return LBM_ERR_ARG;
+    if (lbm_status st = s->ready()) return st;
+    if (!s->initialized) return s->fail(LBM_ERR_STATE, "lbm_mass before lbm_init_phi");
+    long long nb = (s->d.N + 255) / 256;
+    const int nblocks = (int)(nb < kPartBlocks ? nb : kPartBlocks);
+    double h[2];
+    LBM_CK(s, s->ops->mass(s->d, s->level(s->cur), s->part(), nblocks, s->out(), s->stream));
+    LBM_CK(s, cudaMemcpyAsync(h, s->out(), sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+    LBM_CK(s, cudaStreamSynchronize(s->stream));
+    if (mass) *mass = h[0];
+    if (phi_total) *phi_total = h[1];
+    if (!std::isfinite(h[0]) || !std::isfinite(h[1]))
+        return s->fail(LBM_ERR_NONFINITE, "non-finite mass or phi total");
+    return LBM_OK;
+}
+
+lbm_status lbm_laplace(lbm_sim *s, double xc, double yc, double R, double *dP, double *R_eff) {
+    if (!s) return LBM_ERR_ARG;
+    if (lbm_status st = s->ready()) return st;
+    if (!s->initialized) return s->fail(LBM_ERR_STATE, "lbm_laplace before lbm_init_phi");
+    LBM_CK(s, s->ops->fields(s->d, s->level(s->cur), s->slot(0), nullptr, nullptr, nullptr,
+                             nullptr, nullptr, s->slot(6), s->stream));
+    long long nb = (s->d.N + 255) / 256;
+    const int nblocks = (int)(nb < kPartBlocks ? nb : kPartBlocks);
+    const double W = s->prm.W;
+    double h[5];
+    LBM_CK(s, s->ops->laplace(s->d, s->slot(6), s->slot(0), xc, yc, R - 2.0 * W, R + 2.0 * W,
+                              s->part(), nblocks, s->out(), s->stream));
+    LBM_CK(s, cudaMemcpyAsync(h, s->out(), sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+    LBM_CK(s, cudaStreamSynchronize(s->stream));
+    if (dP) *dP = (h[1] > 0 && h[3] > 0) ? h[0] / h[1] - h[2] / h[3] : NAN;
+    if (R_eff) *R_eff = std::sqrt(h[4] / 3.14159265358979323846);
+    if (!std::isfinite(h[0]) || !std::isfinite(h[2]) || !std::isfinite(h[4]))
+        return s->fail(LBM_ERR_NONFINITE, "non-finite pressure or phi");
+    return LBM_OK;
+}
+
+size_t lbm_state_bytes(const lbm_sim *s) { return s ? s->ops->level_bytes(s->d.NS) : 0; }
+
+lbm_status lbm_get_state(lbm_sim *s, void *dst, int on_host, int64_t *step) {
+    if (!s) return LBM_ERR_ARG;
+    if (lbm_status st = s->ready()) return st;
+    if (!s->initialized) return s->fail(LBM_ERR_STATE, "lbm_get_state before lbm_init_phi");
+    if (!dst) return s->fail(LBM_ERR_ARG, "null destination");
+    LBM_CK(s, cudaMemcpyAsync(dst, s->level(s->cur), lbm_state_bytes(s),
+                              on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                              s->stream));
+    if (on_host) LBM_CK(s, cudaStreamSynchronize(s->stream));
+    if (step) *step = s->steps;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_state(lbm_sim *s, const void *src, int on_host, int64_t step) {
+    if (!s) return LBM_ERR_ARG;
+    if (lbm_status st = s->ready()) return st;
+    if (!src) return s->fail(LBM_ERR_ARG, "null source");
+    s->cur = 0;
+    LBM_CK(s, cudaMemcpyAsync(s->level(0), src, lbm_state_bytes(s),
+                              on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                              s->stream));
+    if (on_host) LBM_CK(s, cudaStreamSynchronize(s->stream));
+    s->steps = step;
+    s->initialized = true;
+    return LBM_OK;
+}
+
+int64_t lbm_step_count(const lbm_sim *s) { return s ? s->steps : 0; }
+
+const char *lbm_last_error(const lbm_sim *s) { return s ? s->err.c_str() : "null handle"; }
+
+const char *lbm_create_error(void) { return g_create_err.c_str(); }
+
+void lbm_destroy(lbm_sim *s) { delete s; }
+
+}  // extern "C"

@@ -1,0 +1,6 @@
+// FP32 instantiation: populations and arithmetic in FP32.
+#include "lbm_ops.cuh"
+
+namespace lbm {
+const Ops *ops_f32() { return OpsImpl<float, PlainStore<float>, 2>::ops("f32"); }
+}  // namespace lbm

@@ -1,0 +1,42 @@
+// lbm_internal.h — interface between the C ABI (lbm_api.cu) and the
+// per-storage-type kernel translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace lbm {
+
+// Host-side derived parameters of one domain (FP64).
+struct Derived {
+    int nx, ny, wall;
+    long long N, NS;  // cell count and padded slot stride
+    double phiA, phiB, phibar, rhoB, drho;
+    double kappa, beta, alpha, lambda, gamma;
+    double grav, rhoref, tau_f, tau_g, uwb, uwt;
+};
+
+// Launchers of one storage type.  All are asynchronous on `s` and return
+// the launch status (cudaGetLastError).
+struct Ops {
+    const char *name;
+    size_t field_size;  // bytes of one field element (8 for FP64, else 4)
+    size_t (*level_bytes)(long long NS);
+    cudaError_t (*step)(const Derived &, const void *src, void *dst, cudaStream_t s);
+    cudaError_t (*fields)(const Derived &, const void *lvl, void *phi, void *rho, void *p,
+                          void *ux, void *uy, void *mu, void *P, cudaStream_t s);
+    cudaError_t (*init)(const Derived &, const void *phi0, const void *ux0, const void *uy0,
+                        void *lvl, cudaStream_t s);
+    cudaError_t (*mass)(const Derived &, const void *lvl, double *part, int nblocks,
+                        double *out2, cudaStream_t s);
+    cudaError_t (*laplace)(const Derived &, const void *P, const void *phi, double xc, double yc,
+                           double rin, double rout, double *part, int nblocks, double *out5,
+                           cudaStream_t s);
+};
+
+const Ops *ops_f64();
+const Ops *ops_f32();
+const Ops *ops_f16s();
+const Ops *ops_bf16s();
+
+}  // namespace lbm

@@ -1,0 +1,120 @@
+// lbm_ops.cuh — launchers of the kernels of lbm_kernels.cuh for one
+// (compute type, storage type, tile height) choice.
+#pragma once
+
+#include "lbm_internal.h"
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+template <class T>
+inline KP<T> make_kp(const Derived &d) {
+    KP<T> k;
+    k.nx = d.nx;
+    k.ny = d.ny;
+    k.wall = d.wall;
+    k.NS = d.NS;
+    k.phiA = T(d.phiA);
+    k.phiB = T(d.phiB);
+    k.phibar = T(d.phibar);
+    k.rhoB = T(d.rhoB);
+    k.drho = T(d.drho);
+    k.kappa = T(d.kappa);
+    k.beta4 = T(4.0 * d.beta);
+    k.beta = T(d.beta);
+    k.alpha = T(d.alpha);
+    k.gl = T(d.gamma * d.lambda);
+    k.grav = T(d.grav);
+    k.rhoref = T(d.rhoref);
+    k.itf = T(1.0 / d.tau_f);
+    k.itg = T(1.0 / d.tau_g);
+    k.pf = T(1.0 - 0.5 / d.tau_f);
+    k.pg = T(1.0 - 0.5 / d.tau_g);
+    k.uwb = T(d.uwb);
+    k.uwt = T(d.uwt);
+    return k;
+}
+
+template <class T, class ST, int RPT>
+struct OpsImpl {
+    static constexpr int TY = 8 * RPT;
+    using TL = Tile<T, TY>;
+
+    template <int MODE>
+    static cudaError_t prepare() {
+        // Opt in to more than 48 KB of dynamic shared memory when needed,
+        // once per device.
+        if (TL::bytes <= 48 * 1024) return cudaSuccess;
+        static bool done[64] = {};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 64 && done[dev]) return cudaSuccess;
+        e = cudaFuncSetAttribute(k_step<T, ST, RPT, MODE>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::bytes);
+        if (e == cudaSuccess && dev < 64) done[dev] = true;
+        return e;
+    }
+
+    static dim3 grid(const Derived &d) {
+        return dim3((unsigned)((d.nx + TL::TX - 1) / TL::TX), (unsigned)((d.ny + TY - 1) / TY));
+    }
+
+    static cudaError_t step(const Derived &d, const void *src, void *dst, cudaStream_t s) {
+        cudaError_t e = prepare<MODE_STEP>();
+        if (e != cudaSuccess) return e;
+        k_step<T, ST, RPT, MODE_STEP><<<grid(d), dim3(32, 8), TL::bytes, s>>>(
+            static_cast<const char *>(src), static_cast<char *>(dst), make_kp<T>(d),
+            FieldOut<T>{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr});
+        return cudaGetLastError();
+    }
+
+    static cudaError_t fields(const Derived &d, const void *lvl, void *phi, void *rho, void *p,
+                              void *ux, void *uy, void *mu, void *P, cudaStream_t s) {
+        cudaError_t e = prepare<MODE_FIELDS>();
+        if (e != cudaSuccess) return e;
+        FieldOut<T> o{static_cast<T *>(phi), static_cast<T *>(rho), static_cast<T *>(p),
+                      static_cast<T *>(ux),  static_cast<T *>(uy),  static_cast<T *>(mu),
+                      static_cast<T *>(P)};
+        k_step<T, ST, RPT, MODE_FIELDS><<<grid(d), dim3(32, 8), TL::bytes, s>>>(
+            static_cast<const char *>(lvl), nullptr, make_kp<T>(d), o);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t init(const Derived &d, const void *phi0, const void *ux0, const void *uy0,
+                            void *lvl, cudaStream_t s) {
+        long long nb = (d.N + 255) / 256;
+        if (nb > 152 * 16) nb = 152 * 16;
+        k_init<T, ST><<<(unsigned)nb, 256, 0, s>>>(
+            static_cast<const T *>(phi0), static_cast<const T *>(ux0),
+            static_cast<const T *>(uy0), static_cast<char *>(lvl), make_kp<T>(d));
+        return cudaGetLastError();
+    }
+
+    static cudaError_t mass(const Derived &d, const void *lvl, double *part, int nblocks,
+                            double *out2, cudaStream_t s) {
+        k_mass_partial<T, ST><<<nblocks, 256, 0, s>>>(static_cast<const char *>(lvl),
+                                                      make_kp<T>(d), part);
+        k_reduce_final<<<1, 32, 0, s>>>(part, nblocks, 2, out2);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t laplace(const Derived &d, const void *P, const void *phi, double xc,
+                               double yc, double rin, double rout, double *part, int nblocks,
+                               double *out5, cudaStream_t s) {
+        k_laplace_partial<T><<<nblocks, 256, 0, s>>>(static_cast<const T *>(P),
+                                                     static_cast<const T *>(phi), make_kp<T>(d),
+                                                     xc, yc, rin, rout, part);
+        k_reduce_final<<<1, 32, 0, s>>>(part, nblocks, 5, out5);
+        return cudaGetLastError();
+    }
+
+    static size_t level_bytes(long long NS) { return ST::level_bytes(NS); }
+
+    static const Ops *ops(const char *name) {
+        static const Ops o = {name, sizeof(T), &level_bytes, &step, &fields, &init, &mass, &laplace};
+        return &o;
+    }
+};
+
+}  // namespace lbm

@@ -1,0 +1,263 @@
+"""Thin ctypes binding of the C ABI in ``include/lbm.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA
+kernels of ``liblbm.so``.  PyTorch provides the device memory (two caller-
+owned buffers) and the stream.  There is no CPU fallback: loading fails
+loudly when the library is missing or no GPU is present.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbm.so")
+
+F64, F32, F16S, BF16S = 0, 1, 2, 3
+PERIODIC, WALL = 0, 1
+DTYPES = {"f64": F64, "f32": F32, "f16s": F16S, "bf16s": BF16S}
+
+STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_NONFINITE",
+          -4: "LBM_ERR_TIMEOUT", -5: "LBM_ERR_STATE", -6: "LBM_ERR_NOMEM"}
+
+# Every entry point declared in include/lbm.h.
+EXPORTS = ["lbm_version", "lbm_buffer_sizes", "lbm_create", "lbm_bind_buffers", "lbm_init_phi",
+           "lbm_step", "lbm_fields", "lbm_mass", "lbm_laplace", "lbm_state_bytes",
+           "lbm_get_state", "lbm_set_state", "lbm_step_count", "lbm_last_error",
+           "lbm_create_error", "lbm_destroy"]
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CParams(ctypes.Structure):
+    """Mirror of lbm_params (include/lbm.h)."""
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("rho_A", ctypes.c_double), ("rho_B", ctypes.c_double),
+        ("phi_A", ctypes.c_double), ("phi_B", ctypes.c_double),
+        ("sigma", ctypes.c_double), ("W", ctypes.c_double), ("M", ctypes.c_double),
+        ("tau_f", ctypes.c_double), ("tau_g", ctypes.c_double),
+        ("gravity", ctypes.c_double), ("rho_ref", ctypes.c_double),
+        ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
+        ("u_wall_bottom", ctypes.c_double), ("u_wall_top", ctypes.c_double),
+        ("dtype", ctypes.c_int),
+    ]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def load(path: str = LIB_PATH):
+    """Load liblbm.so (no build, no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    S = ctypes.c_int
+    lib.lbm_version.restype = ctypes.c_int
+    lib.lbm_buffer_sizes.restype = S
+    lib.lbm_buffer_sizes.argtypes = [ctypes.POINTER(CParams), ctypes.POINTER(ctypes.c_size_t),
+                                     ctypes.POINTER(ctypes.c_size_t)]
+    lib.lbm_create.restype = S
+    lib.lbm_create.argtypes = [ctypes.POINTER(CParams), _vp, ctypes.POINTER(_vp)]
+    lib.lbm_bind_buffers.restype = S
+    lib.lbm_bind_buffers.argtypes = [_vp, _vp, ctypes.c_size_t, _vp, ctypes.c_size_t]
+    lib.lbm_init_phi.restype = S
+    lib.lbm_init_phi.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int]
+    lib.lbm_step.restype = S
+    lib.lbm_step.argtypes = [_vp, ctypes.c_int64]
+    lib.lbm_fields.restype = S
+    lib.lbm_fields.argtypes = [_vp] + [_vp] * 6 + [ctypes.c_int]
+    lib.lbm_mass.restype = S
+    lib.lbm_mass.argtypes = [_vp, _dp, _dp]
+    lib.lbm_laplace.restype = S
+    lib.lbm_laplace.argtypes = [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp]
+    lib.lbm_state_bytes.restype = ctypes.c_size_t
+    lib.lbm_state_bytes.argtypes = [_vp]
+    lib.lbm_get_state.restype = S
+    lib.lbm_get_state.argtypes = [_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
+    lib.lbm_set_state.restype = S
+    lib.lbm_set_state.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int64]
+    lib.lbm_step_count.restype = ctypes.c_int64
+    lib.lbm_step_count.argtypes = [_vp]
+    lib.lbm_last_error.restype = ctypes.c_char_p
+    lib.lbm_last_error.argtypes = [_vp]
+    lib.lbm_create_error.restype = ctypes.c_char_p
+    lib.lbm_destroy.restype = None
+    lib.lbm_destroy.argtypes = [_vp]
+    _lib = lib
+    return lib
+
+
+def make_params(d: dict, dtype) -> CParams:
+    """lbm_params from a parameter dict in the paper's notation."""
+    if isinstance(dtype, str):
+        dtype = DTYPES[dtype]
+    keys = [f[0] for f in CParams._fields_ if f[0] != "dtype"]
+    return CParams(*[d[k] for k in keys], dtype)
+
+
+def buffer_sizes(d: dict, dtype):
+    lib = load()
+    cp = make_params(d, dtype)
+    sb, wb = ctypes.c_size_t(), ctypes.c_size_t()
+    st = lib.lbm_buffer_sizes(ctypes.byref(cp), ctypes.byref(sb), ctypes.byref(wb))
+    if st != 0:
+        raise LBMError(st, lib.lbm_create_error().decode())
+    return sb.value, wb.value
+
+
+class Sim:
+    """One domain on the current CUDA device.
+
+    ``params`` is a dict in the paper's notation (see workloads.py);
+    ``dtype`` one of "f64", "f32", "f16s", "bf16s".  Buffers are torch
+    tensors owned by this object; the stream is torch's current stream at
+    construction unless one is given.
+    """
+
+    def __init__(self, params: dict, dtype="f32", stream=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblbm needs a CUDA device; none is available")
+        self._lib = load()
+        self.params = dict(params)
+        self.dtype = dtype if isinstance(dtype, str) else {v: k for k, v in DTYPES.items()}[dtype]
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.field_dtype = torch.float64 if self.dtype == "f64" else torch.float32
+        self.shape = (params["ny"], params["nx"])
+        self._cp = make_params(params, self.dtype)
+        h = _vp()
+        st = self._lib.lbm_create(ctypes.byref(self._cp), _vp(self.stream.cuda_stream),
+                                  ctypes.byref(h))
+        if st != 0:
+            raise LBMError(st, self._lib.lbm_create_error().decode())
+        self._h = h
+        sb, wb = buffer_sizes(params, self.dtype)
+        self.state_buf = torch.empty(sb, dtype=torch.uint8, device=self.device)
+        self.work_buf = torch.empty(wb, dtype=torch.uint8, device=self.device)
+        self._check(self._lib.lbm_bind_buffers(h, self.state_buf.data_ptr(), sb,
+                                               self.work_buf.data_ptr(), wb))
+
+    # -- plumbing
+    def _check(self, st):
+        if st != 0:
+            raise LBMError(st, self._lib.lbm_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- API
+    def _field_tensor(self, a):
+        import torch
+        if a is None:
+            return None
+        if isinstance(a, np.ndarray):
+            a = torch.from_numpy(np.ascontiguousarray(a))
+        return a.to(device=self.device, dtype=self.field_dtype).contiguous().reshape(self.shape)
+
+    def init_phi(self, phi, ux=None, uy=None):
+        """Equilibrium initial state from phi (and optional u): device path."""
+        t = [self._field_tensor(a) for a in (phi, ux, uy)]
+        self._keep = t  # inputs must live until the stream consumes them
+        ptr = [None if a is None else a.data_ptr() for a in t]
+        self._check(self._lib.lbm_init_phi(self._h, ptr[0], ptr[1], ptr[2], 0))
+
+    def init_phi_host(self, phi, ux=None, uy=None):
+        """Same from host numpy arrays (copied in by the library)."""
+        npdt = np.float64 if self.dtype == "f64" else np.float32
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=npdt).reshape(self.shape)
+                for a in (phi, ux, uy)]
+        ptr = [None if a is None else a.ctypes.data for a in arrs]
+        self._check(self._lib.lbm_init_phi(self._h, ptr[0], ptr[1], ptr[2], 1))
+
+    def step(self, n: int = 1):
+        self._check(self._lib.lbm_step(self._h, int(n)))
+
+    @property
+    def step_count(self) -> int:
+        return self._lib.lbm_step_count(self._h)
+
+    def fields(self, names=("phi", "rho", "p", "ux", "uy", "mu")):
+        """Device tensors of the current macroscopic fields."""
+        import torch
+        order = ("phi", "rho", "p", "ux", "uy", "mu")
+        out = {k: torch.empty(self.shape, dtype=self.field_dtype, device=self.device)
+               for k in names}
+        ptr = [out[k].data_ptr() if k in out else None for k in order]
+        self._check(self._lib.lbm_fields(self._h, *ptr, 0))
+        return out
+
+    def fields_host(self, names=("phi", "rho", "p", "ux", "uy", "mu"), out=None):
+        """Host numpy copies of the current fields (library copies out)."""
+        order = ("phi", "rho", "p", "ux", "uy", "mu")
+        npdt = np.float64 if self.dtype == "f64" else np.float32
+        if out is None:
+            out = {k: np.empty(self.shape, dtype=npdt) for k in names}
+        ptr = [out[k].ctypes.data if k in out else None for k in order]
+        self._check(self._lib.lbm_fields(self._h, *ptr, 1))
+        return out
+
+    def mass(self):
+        m, t = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.lbm_mass(self._h, ctypes.byref(m), ctypes.byref(t)))
+        return m.value, t.value
+
+    def laplace(self, xc, yc, R):
+        dP, Re = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.lbm_laplace(self._h, float(xc), float(yc), float(R),
+                                          ctypes.byref(dP), ctypes.byref(Re)))
+        return dP.value, Re.value
+
+    def state_bytes(self) -> int:
+        return self._lib.lbm_state_bytes(self._h)
+
+    def get_state(self):
+        import torch
+        buf = torch.empty(self.state_bytes(), dtype=torch.uint8, device=self.device)
+        step = ctypes.c_int64()
+        self._check(self._lib.lbm_get_state(self._h, buf.data_ptr(), 0, ctypes.byref(step)))
+        return buf, step.value
+
+    def set_state(self, buf, step: int):
+        self._check(self._lib.lbm_set_state(self._h, buf.data_ptr(), 0, int(step)))
+
+
+@dataclass
+class HostRun:
+    fields: dict
+    mass: tuple
+
+
+def run_host(params: dict, phi0: np.ndarray, steps: int, dtype="f32", ux0=None, uy0=None,
+             names=("phi", "ux", "uy", "p")) -> HostRun:
+    """End-to-end call with host buffers: copy phi0 in, step, copy fields out."""
+    sim = Sim(params, dtype)
+    try:
+        sim.init_phi_host(phi0, ux0, uy0)
+        sim.step(steps)
+        out = sim.fields_host(names)
+        return HostRun(out, sim.mass())
+    finally:
+        sim.close()
