@@ -163,12 +163,45 @@ LBM_API int64_t lbm_step_count(const lbm_sim *sim);
  * call on the handle. */
 LBM_API const char *lbm_last_error(const lbm_sim *sim);
 
-/* Message of the last lbm_create / lbm_buffer_sizes failure in this
- * thread (those calls have no handle to store it in). */
+/* Message of the last lbm_create / lbm_buffer_sizes / lbm_mass_noalloc
+ * failure in this thread (those calls have no handle to store it in). */
 LBM_API const char *lbm_create_error(void);
 
 /* Free the handle's host state.  Bound buffers stay the caller's. */
 LBM_API void lbm_destroy(lbm_sim *sim);
+
+/* The mass diagnostic of lbm_mass for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a library convenience.
+ *
+ * lbm_mass keeps its reduction partials in the work buffer the caller binds
+ * to a handle.  Callers whose device memory is a fixed budget owned by
+ * someone else, plug-ins that must not grow the process's device footprint,
+ * and loops that cannot take cudaMalloc's implicit device-wide
+ * synchronisation have no such buffer to give.  This entry point needs none
+ * and no handle: its scratch is a static 64 KB device array inside the
+ * library (every GPU that loads the library holds it until the process
+ * exits), and it calls no allocating routine.
+ *
+ *   prm        parameters of the domain (validated as by lbm_buffer_sizes)
+ *   level      device pointer to ONE time level of populations in the
+ *              library's layout for prm->dtype, e.g. what lbm_get_state
+ *              writes (read only)
+ *   stream     cudaStream_t to run on; it is synchronised before return
+ *   mass, phi_total  host outputs (either may be NULL): sum rho and sum phi,
+ *              accumulated in FP64 in a fixed order
+ *
+ * Limits and errors: grids of at most 2^28 cells (16384 x 16384); larger
+ * grids return LBM_ERR_NOMEM without touching the GPU.  LBM_ERR_ARG for
+ * invalid parameters or a NULL level, LBM_ERR_NONFINITE for NaN/Inf sums,
+ * LBM_ERR_CUDA for a failed CUDA call; lbm_create_error() gives the
+ * message.  The first call on each device looks up the scratch array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls in the process share the one scratch array,
+ * which keeps the last call's contents (each call writes every slot it
+ * reads, so nothing needs clearing): calls that overlap on the GPU, from
+ * any thread or stream, race with each other. */
+LBM_API lbm_status lbm_mass_noalloc(const lbm_params *prm, const void *level, void *stream,
+                                    double *mass, double *phi_total);
 
 #ifdef __cplusplus
 }

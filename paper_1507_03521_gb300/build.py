@@ -26,6 +26,7 @@ UNITS = {
     "lbm_f64": ["-fmad=false"],
     "lbm_f32": [],
     "lbm_f16": [],
+    "lbm_noalloc": [],
 }
 
 

@@ -102,6 +102,8 @@ Layout layout(const Derived &d, const Ops *ops) {
 
 }  // namespace
 
+void lbm_internal_set_error(const char *msg) { g_create_err = msg ? msg : ""; }
+
 struct lbm_sim {
     lbm_params prm;
     Derived d;

@@ -40,3 +40,7 @@ const Ops *ops_f16s();
 const Ops *ops_bf16s();
 
 }  // namespace lbm
+
+// Records a message for lbm_create_error() in the calling thread (used by
+// entry points that have no handle to store it in).
+void lbm_internal_set_error(const char *msg);

@@ -27,7 +27,7 @@ STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_NONFI
 EXPORTS = ["lbm_version", "lbm_buffer_sizes", "lbm_create", "lbm_bind_buffers", "lbm_init_phi",
            "lbm_step", "lbm_fields", "lbm_mass", "lbm_laplace", "lbm_state_bytes",
            "lbm_get_state", "lbm_set_state", "lbm_step_count", "lbm_last_error",
-           "lbm_create_error", "lbm_destroy"]
+           "lbm_create_error", "lbm_destroy", "lbm_mass_noalloc"]
 
 
 class LBMError(RuntimeError):
@@ -97,6 +97,8 @@ def load(path: str = LIB_PATH):
     lib.lbm_create_error.restype = ctypes.c_char_p
     lib.lbm_destroy.restype = None
     lib.lbm_destroy.argtypes = [_vp]
+    lib.lbm_mass_noalloc.restype = S
+    lib.lbm_mass_noalloc.argtypes = [ctypes.POINTER(CParams), _vp, _vp, _dp, _dp]
     _lib = lib
     return lib
 
