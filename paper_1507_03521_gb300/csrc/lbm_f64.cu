@@ -3,5 +3,5 @@
 #include "lbm_ops.cuh"
 
 namespace lbm {
-const Ops *ops_f64() { return OpsImpl<double, PlainStore<double>, 2>::ops("f64"); }
+const Ops *ops_f64() { return OpsImpl<double, PlainStore<double>, 2, 64, 1>::ops("f64"); }
 }  // namespace lbm

@@ -4,6 +4,7 @@
 
 #include "lbm_internal.h"
 #include "lbm_kernels.cuh"
+#include "lbm_strip.cuh"
 
 namespace lbm {
 
@@ -35,10 +36,52 @@ inline KP<T> make_kp(const Derived &d) {
     return k;
 }
 
-template <class T, class ST, int RPT>
+template <class T, class ST, int RPT, int SW, int DEPTH>
 struct OpsImpl {
     static constexpr int TY = 8 * RPT;
     using TL = Tile<T, TY>;
+    using SM = StripSmem<T, ST, SW, DEPTH>;
+
+    // The strip kernel needs 16-byte aligned rows: nx a multiple of 8.
+    static bool strip_ok(const Derived &d) { return d.nx % 8 == 0; }
+
+    struct StripCfg {
+        bool ready = false;
+        int per_sm = 0, sms = 0;
+    };
+
+    // Opt in to the strip kernel's shared memory and size the grid to
+    // one wave: strips x segments ~= resident CTAs, segments >= 16 rows.
+    static cudaError_t strip_grid(const Derived &d, dim3 &grid, int &seg_h) {
+        static StripCfg cfg[64];
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev >= 64) return cudaErrorInvalidDevice;
+        StripCfg &c = cfg[dev];
+        if (!c.ready) {
+            e = cudaFuncSetAttribute(k_strip<T, ST, SW, DEPTH>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
+            if (e != cudaSuccess) return e;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.per_sm, k_strip<T, ST, SW, DEPTH>,
+                                                              SW, SM::bytes);
+            if (e != cudaSuccess) return e;
+            e = cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+            if (c.per_sm < 1) return cudaErrorInvalidConfiguration;
+            c.ready = true;
+        }
+        const int strips = (d.nx + SW - 1) / SW;
+        long long slots = (long long)c.per_sm * c.sms;
+        long long nseg = slots / strips;
+        if (nseg < 1) nseg = 1;
+        const long long max_seg = (d.ny + 15) / 16;
+        if (nseg > max_seg) nseg = max_seg;
+        seg_h = (int)((d.ny + nseg - 1) / nseg);
+        nseg = (d.ny + seg_h - 1) / seg_h;
+        grid = dim3((unsigned)strips, (unsigned)nseg);
+        return cudaSuccess;
+    }
 
     template <int MODE>
     static cudaError_t prepare() {
@@ -61,6 +104,15 @@ struct OpsImpl {
     }
 
     static cudaError_t step(const Derived &d, const void *src, void *dst, cudaStream_t s) {
+        if (strip_ok(d)) {
+            dim3 grid;
+            int seg_h = 0;
+            cudaError_t e = strip_grid(d, grid, seg_h);
+            if (e != cudaSuccess) return e;
+            k_strip<T, ST, SW, DEPTH><<<grid, SW, SM::bytes, s>>>(
+                static_cast<const char *>(src), static_cast<char *>(dst), make_kp<T>(d), seg_h);
+            return cudaGetLastError();
+        }
         cudaError_t e = prepare<MODE_STEP>();
         if (e != cudaSuccess) return e;
         k_step<T, ST, RPT, MODE_STEP><<<grid(d), dim3(32, 8), TL::bytes, s>>>(

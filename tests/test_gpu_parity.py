@@ -49,6 +49,7 @@ def _run_orc(p, phi, ux, uy, steps):
     return o.fields(), o.mass(), o
 
 
+# Grids with nx % 8 == 0 run the strip kernel; the others the tile kernel.
 CASES = [
     ("tiny5x5", lambda: W.small_case(5, 5, seed=1), 10),
     ("odd6x7", lambda: W.small_case(6, 7, seed=2), 10),
@@ -59,6 +60,11 @@ CASES = [
     ("walls33x34", lambda: W.small_case(33, 34, seed=7, walls=True, gravity=1e-5, u_wall=0.01), 20),
     ("droplet64", lambda: W.droplet64() + (None, None), 50),
     ("zero_steps", lambda: W.small_case(40, 24, seed=8), 0),
+    ("strip32x29", lambda: W.small_case(32, 29, seed=14), 20),
+    ("strip136x37", lambda: W.small_case(136, 37, seed=15), 20),
+    ("strip_walls24x5", lambda: W.small_case(24, 5, seed=16, walls=True, gravity=1e-5, u_wall=0.02), 15),
+    ("strip_walls200x45", lambda: W.small_case(200, 45, seed=17, walls=True, gravity=2e-5, u_wall=-0.01), 25),
+    ("strip_walls8x70", lambda: W.small_case(8, 70, seed=18, walls=True, gravity=1e-5, u_wall=0.01), 20),
 ]
 
 
@@ -182,9 +188,10 @@ def test_conservation_long_f64(lbm):
     assert abs(t1 - t0) <= 1e-13 * np.abs(phi).sum()
 
 
-def test_resume_is_bit_identical(lbm):
-    p, phi, ux, uy = W.small_case(70, 45, seed=10)
-    for dtype in ("f32", "f16s"):
+@pytest.mark.parametrize("shape", [(70, 45), (64, 48)])
+def test_resume_is_bit_identical(lbm, shape):
+    p, phi, ux, uy = W.small_case(shape[0], shape[1], seed=10)
+    for dtype in ("f32", "f16s", "bf16s", "f64"):
         a = lbm.Sim(p, dtype)
         a.init_phi(phi, ux, uy)
         a.step(7)
@@ -200,8 +207,9 @@ def test_resume_is_bit_identical(lbm):
             assert np.array_equal(fa[k], fb[k]), (dtype, k)
 
 
-def test_runs_are_deterministic(lbm):
-    p, phi, ux, uy = W.small_case(70, 45, seed=12)
+@pytest.mark.parametrize("shape", [(70, 45), (64, 48)])
+def test_runs_are_deterministic(lbm, shape):
+    p, phi, ux, uy = W.small_case(shape[0], shape[1], seed=12)
     outs = []
     for _ in range(2):
         s = lbm.Sim(p, "f32")
