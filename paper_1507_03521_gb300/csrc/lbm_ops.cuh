@@ -42,8 +42,11 @@ struct OpsImpl {
     using TL = Tile<T, TY>;
     using SM = StripSmem<T, ST, SW, DEPTH>;
 
-    // The strip kernel needs 16-byte aligned rows: nx a multiple of 8.
-    static bool strip_ok(const Derived &d) { return d.nx % 8 == 0; }
+    // The strip kernel needs 16-byte aligned rows (nx a multiple of 8) and
+    // a level that 32-bit element offsets can address.
+    static bool strip_ok(const Derived &d) {
+        return d.nx % 8 == 0 && StripRow<ST, SW>::idx32_ok(d.NS);
+    }
 
     struct StripCfg {
         bool ready = false;

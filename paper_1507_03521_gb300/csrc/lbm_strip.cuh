@@ -1,5 +1,5 @@
 // lbm_strip.cuh — the streaming form of the time step, for grids whose nx
-// is a multiple of 8.
+// is a multiple of 8 (and whose level fits 32-bit element offsets).
 //
 // Same arithmetic as k_step (lbm_kernels.cuh), reorganised so that the
 // radius-3 coupling of the step (grad p <- p <- lap mu <- lap phi) costs
@@ -11,7 +11,9 @@
 //       3. mu        at row y+2 (Eq. 5),
 //       4. u, p, F, lap mu, grad phi at row y+1 (Eqs. 31-32),
 //       5. collides row y (Eqs. 22-29) and pushes it to the other level.
-//     Rows of phi, mu, p and u live in small shared-memory rings.
+//     Rows of phi, mu, p and u live in small shared-memory rings.  The
+//     halo columns of steps 1-4 are spread over different warps so that no
+//     warp carries all the extra passes into the next barrier.
 //   * Population rows are copied global -> shared with cp.async (16-byte
 //     chunks, L2 only) DEPTH rows ahead of use, so DRAM traffic overlaps the
 //     arithmetic of the rows in flight.  Every population is read from DRAM
@@ -48,81 +50,130 @@ __device__ __forceinline__ int wrap_any(int x, int nx) {
     return x;
 }
 
-// Shared-memory row buffers of the populations, per storage type.
-template <class ST>
+__device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
+
+// Shared-memory row buffers of the populations, per storage type.  A row
+// buffer holds columns x0-HP .. x0+SW+HP-1 of every slot; the async copy of
+// a row is described once per thread (which 16-byte chunks it copies) and
+// replayed for every row with only the row offset changing.
+template <class ST, int SW>
 struct StripRow;
 
-template <class T>
-struct StripRow<PlainStore<T>> {
+template <class T, int SW>
+struct StripRow<PlainStore<T>, SW> {
     using C = T;
     static constexpr int HP = 4;               // halo columns loaded each side
+    static constexpr int LW = SW + 2 * HP;     // row width
     static constexpr int CE = 16 / sizeof(T);  // elements per 16-byte chunk
-    template <int LW>
-    static constexpr size_t bytes() { return (size_t)18 * LW * sizeof(T); }
-    // Issue the async copy of global row `srow`, columns x_start .. x_start+LW-1
-    // (wrapped periodically), of all 18 slots into sbuf.
-    template <int LW>
-    __device__ __forceinline__ static void issue(char *sbuf, const char *lvl, long long NS,
-                                                 long long rowbase, int x_start, int nx, int tid,
-                                                 int nthr) {
-        constexpr int CPS = LW / CE;  // chunks per slot
-        const T *g = reinterpret_cast<const T *>(lvl);
-        T *s = reinterpret_cast<T *>(sbuf);
-        for (int j = tid; j < 18 * CPS; j += nthr) {
-            const int sl = j / CPS, c = j - sl * CPS;
-            const int xw = wrap_any(x_start + c * CE, nx);
-            cp_async16(s + sl * LW + c * CE, g + sl * NS + rowbase + xw);
+    static constexpr int CPS = LW / CE;        // chunks per slot
+    static constexpr int TOTAL = 18 * CPS;
+    static constexpr int NCH = (TOTAL + SW - 1) / SW;
+    static constexpr size_t bytes = (size_t)18 * LW * sizeof(T);
+    static bool idx32_ok(long long NS) { return 18 * NS < (1LL << 31); }
+
+    struct Desc {
+        int goff[NCH], soff[NCH];
+    };
+    __device__ __forceinline__ static void describe(Desc &d, int t, long long NS, int x_start,
+                                                    int nx) {
+#pragma unroll
+        for (int k = 0; k < NCH; ++k) {
+            const int j = t + k * SW;
+            if (j < TOTAL) {
+                const int sl = j / CPS, c = j - sl * CPS;
+                d.goff[k] = sl * (int)NS + wrap_any(x_start + c * CE, nx);
+                d.soff[k] = sl * LW + c * CE;
+            } else {
+                d.goff[k] = -1;
+                d.soff[k] = 0;
+            }
         }
     }
-    template <int LW>
+    __device__ __forceinline__ static void issue(const Desc &d, char *sbuf, const char *lvl,
+                                                 int rowbase) {
+        const T *g = reinterpret_cast<const T *>(lvl);
+        T *s = reinterpret_cast<T *>(sbuf);
+#pragma unroll
+        for (int k = 0; k < NCH; ++k)
+            if (d.goff[k] >= 0) cp_async16(s + d.soff[k], g + (d.goff[k] + rowbase));
+    }
     __device__ __forceinline__ static void read_f(const char *sbuf, int c, C f[9]) {
         const T *s = reinterpret_cast<const T *>(sbuf);
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = s[i * LW + c];
     }
-    template <int LW>
     __device__ __forceinline__ static void read_g(const char *sbuf, int c, C g[9]) {
         const T *s = reinterpret_cast<const T *>(sbuf);
 #pragma unroll
         for (int i = 0; i < 9; ++i) g[i] = s[(9 + i) * LW + c];
     }
+    // Interior push: slot i of cell kb + cy_i nx + cx_i, 32-bit offsets.
+    __device__ __forceinline__ static void store_fast(char *lvl, int NS, int nx, int kb,
+                                                      const C fv[9], const C gv[9], C) {
+        T *b = reinterpret_cast<T *>(lvl) + kb;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) b[i * NS + D2Q9::cy(i) * nx + D2Q9::cx(i)] = fv[i];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) b[(9 + i) * NS + D2Q9::cy(i) * nx + D2Q9::cx(i)] = gv[i];
+    }
 };
 
-template <class H>
-struct StripRow<Store16<H>> {
+template <class H, int SW>
+struct StripRow<Store16<H>, SW> {
     using C = float;
     using E = HalfStore<H>;
     static constexpr int HP = 8;  // 8 halves per 16-byte chunk
-    template <int LW>
-    static constexpr size_t bytes() { return (size_t)LW * 4 + (size_t)17 * LW * 2; }
-    template <int LW>
-    __device__ __forceinline__ static void issue(char *sbuf, const char *lvl, long long NS,
-                                                 long long rowbase, int x_start, int nx, int tid,
-                                                 int nthr) {
-        constexpr int C0 = LW / 4, CH = LW / 8;  // chunks: g0 (floats), each half slot
-        const float *g0 = reinterpret_cast<const float *>(lvl);
-        const unsigned short *h = reinterpret_cast<const unsigned short *>(lvl + NS * 4);
-        float *s0 = reinterpret_cast<float *>(sbuf);
-        unsigned short *sh = reinterpret_cast<unsigned short *>(sbuf + (size_t)LW * 4);
-        for (int j = tid; j < C0 + 17 * CH; j += nthr) {
-            if (j < C0) {
-                const int xw = wrap_any(x_start + j * 4, nx);
-                cp_async16(s0 + j * 4, g0 + rowbase + xw);
+    static constexpr int LW = SW + 2 * HP;
+    static constexpr int C0 = LW / 4, CH = LW / 8;  // chunks: g0 row (floats), each half slot
+    static constexpr int N0 = (C0 + SW - 1) / SW, NH = (17 * CH + SW - 1) / SW;
+    static constexpr size_t bytes = (size_t)LW * 4 + (size_t)17 * LW * 2;
+    // half offsets are counted from the level base: the half slots start at
+    // half index 2 NS (after NS floats of g_0)
+    static bool idx32_ok(long long NS) { return 19 * NS < (1LL << 31); }
+
+    struct Desc {
+        int g0off[N0], s0off[N0], hoff[NH], shoff[NH];
+    };
+    __device__ __forceinline__ static void describe(Desc &d, int t, long long NS, int x_start,
+                                                    int nx) {
+#pragma unroll
+        for (int k = 0; k < N0; ++k) {
+            const int j = t + k * SW;
+            d.g0off[k] = j < C0 ? wrap_any(x_start + j * 4, nx) : -1;
+            d.s0off[k] = j * 4;
+        }
+#pragma unroll
+        for (int k = 0; k < NH; ++k) {
+            const int j = t + k * SW;
+            if (j < 17 * CH) {
+                const int sl = j / CH, c = j - sl * CH;
+                d.hoff[k] = (2 + sl) * (int)NS + wrap_any(x_start + c * 8, nx);
+                d.shoff[k] = sl * LW + c * 8;
             } else {
-                const int jj = j - C0;
-                const int sl = jj / CH, c = jj - sl * CH;
-                const int xw = wrap_any(x_start + c * 8, nx);
-                cp_async16(sh + sl * LW + c * 8, h + sl * NS + rowbase + xw);
+                d.hoff[k] = -1;
+                d.shoff[k] = 0;
             }
         }
     }
-    template <int LW>
+    __device__ __forceinline__ static void issue(const Desc &d, char *sbuf, const char *lvl,
+                                                 int rowbase) {
+        const float *g0 = reinterpret_cast<const float *>(lvl);
+        const unsigned short *h = reinterpret_cast<const unsigned short *>(lvl);
+        float *s0 = reinterpret_cast<float *>(sbuf);
+        unsigned short *sh = reinterpret_cast<unsigned short *>(sbuf + (size_t)LW * 4);
+#pragma unroll
+        for (int k = 0; k < N0; ++k)
+            if (d.g0off[k] >= 0) cp_async16(s0 + d.s0off[k], g0 + (d.g0off[k] + rowbase));
+#pragma unroll
+        for (int k = 0; k < NH; ++k)
+            if (d.hoff[k] >= 0) cp_async16(sh + d.shoff[k], h + (d.hoff[k] + rowbase));
+    }
     __device__ __forceinline__ static void read_f(const char *sbuf, int c, C f[9]) {
         const unsigned short *sh = reinterpret_cast<const unsigned short *>(sbuf + (size_t)LW * 4);
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = E::dec(sh[i * LW + c]);
     }
-    template <int LW>
     __device__ __forceinline__ static void read_g(const char *sbuf, int c, C g[9]) {
         const float *s0 = reinterpret_cast<const float *>(sbuf);
         const unsigned short *sh = reinterpret_cast<const unsigned short *>(sbuf + (size_t)LW * 4);
@@ -130,19 +181,34 @@ struct StripRow<Store16<H>> {
 #pragma unroll
         for (int i = 1; i < 9; ++i) g[i] = E::dec(sh[(8 + i) * LW + c]);
     }
+    __device__ __forceinline__ static void store_fast(char *lvl, int NS, int nx, int kb,
+                                                      const C fv[9], const C gv[9], C phi) {
+        float *g0 = reinterpret_cast<float *>(lvl);
+        unsigned short *h = reinterpret_cast<unsigned short *>(lvl + (size_t)NS * 4) + kb;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) h[i * NS + D2Q9::cy(i) * nx + D2Q9::cx(i)] = E::enc(fv[i]);
+        float rest = phi;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const unsigned short q = E::enc(gv[i]);
+            rest -= E::dec(q);
+            h[(8 + i) * NS + D2Q9::cy(i) * nx + D2Q9::cx(i)] = q;
+        }
+        g0[kb] = rest;
+    }
 };
 
 // Shared-memory layout of one strip CTA.
 template <class T, class ST, int SW, int DEPTH>
 struct StripSmem {
-    using SR = StripRow<ST>;
+    using SR = StripRow<ST, SW>;
     static constexpr int HP = SR::HP;
-    static constexpr int LW = SW + 2 * HP;     // population row width
+    static constexpr int LW = SR::LW;
     static constexpr int NB = DEPTH + 4;       // population row buffers
     static constexpr int RPHI = 5, RMU = 4, RP = 3, RU = 2;
     static constexpr int WPHI = SW + 6, WMU = SW + 4, WQ = SW + 2;
-    static constexpr size_t popb = SR::template bytes<LW>();
-    static constexpr size_t pop_bytes = ((popb + 15) / 16 * 16) * NB;
+    static constexpr size_t popb = (SR::bytes + 15) / 16 * 16;
+    static constexpr size_t pop_bytes = popb * NB;
     // fields: phi ring, mu ring, p ring, ps/jx/jy (1 row), and a 2-row ring
     // of ux, uy, Fx, Fy, lap mu, grad phi (x, y)
     static constexpr size_t fld_elems =
@@ -150,7 +216,7 @@ struct StripSmem {
     static constexpr size_t bytes = pop_bytes + fld_elems * sizeof(T);
 
     char *pop;
-    T *phi, *mu, *p, *ps, *jx, *jy, *ux, *uy, *Fx, *Fy, *lmu, *gpx_, *gpy_;
+    T *phi, *mu, *p, *ps, *jx, *jy, *ux, *uy, *Fx, *Fy, *lmu, *gphx, *gphy;
     __device__ __forceinline__ StripSmem(char *base) {
         pop = base;
         phi = reinterpret_cast<T *>(base + pop_bytes);
@@ -164,12 +230,10 @@ struct StripSmem {
         Fx = uy + RU * WQ;
         Fy = Fx + RU * WQ;
         lmu = Fy + RU * WQ;
-        gpx_ = lmu + RU * WQ;   // grad phi, x
-        gpy_ = gpx_ + RU * WQ;  // grad phi, y
+        gphx = lmu + RU * WQ;
+        gphy = gphx + RU * WQ;
     }
-    __device__ __forceinline__ char *buf(int row) const {
-        return pop + (size_t)((row + 64) % NB) * ((popb + 15) / 16 * 16);
-    }
+    __device__ __forceinline__ char *buf(int row) const { return pop + (size_t)((row + 64) % NB) * popb; }
     // ring row pointers; column index relative to the strip's first column
     __device__ __forceinline__ T *phir(int row) const { return phi + ((row + 64) % RPHI) * WPHI + 3; }
     __device__ __forceinline__ T *mur(int row) const { return mu + ((row + 64) % RMU) * WMU + 2; }
@@ -177,66 +241,73 @@ struct StripSmem {
     __device__ __forceinline__ int ur(int row) const { return ((row + 64) % RU) * WQ + 1; }
 };
 
+// Column loop of one step: columns -h .. SW+h-1.  Every thread takes column
+// t - h; the 2h columns past SW-h are taken by the first 2h lanes of warp
+// `xw` (a different warp per step), so no warp carries every extra pass.
+template <int SW, int H, int XW, class F>
+__device__ __forceinline__ void columns(int t, F &&fn) {
+    fn(t - H);
+    constexpr int NW = SW / 32;
+    if ((t >> 5) == (XW % NW) && (t & 31) < 2 * H) fn(SW - H + (t & 31));
+}
+
 template <class T, class ST, int SW, int DEPTH>
 __global__ void __launch_bounds__(SW)
 k_strip(const char *__restrict__ src, char *__restrict__ dst, const KP<T> P, int seg_h) {
     using SM = StripSmem<T, ST, SW, DEPTH>;
     using SR = typename SM::SR;
-    constexpr int LW = SM::LW, HP = SM::HP;
+    constexpr int HP = SM::HP;
     extern __shared__ __align__(16) char smem_raw[];
     const SM s(smem_raw);
     const int t = threadIdx.x;
     const int nx = P.nx, ny = P.ny, wall = P.wall;
-    const long long NS = P.NS;
+    const int NS = (int)P.NS;
     const int x0 = blockIdx.x * SW;
     const int ys = blockIdx.y * seg_h;
     const int ye = min(ys + seg_h, ny);
     const int yfirst = ys - 6;
-    const int xs = x0 - HP;  // first loaded column
+
+    typename SR::Desc desc;
+    SR::describe(desc, t, P.NS, x0 - HP, nx);
+    __syncthreads();
 
     auto issue_row = [&](int row) {
-        if (row <= ye + 2) {
-            const long long rb = (long long)src_row(row, ny, wall) * nx;
-            SR::template issue<LW>(s.buf(row), src, NS, rb, xs, nx, t, SW);
-        }
+        if (row <= ye + 2) SR::issue(desc, s.buf(row), src, src_row(row, ny, wall) * nx);
         cp_async_commit();  // one group per row, possibly empty
     };
-    // Prologue: rows yfirst+3 .. yfirst+3+DEPTH-1.
 #pragma unroll
     for (int d = 0; d < DEPTH; ++d) issue_row(yfirst + 3 + d);
 
+    // Interior strips never wrap in x when pushing; interior rows never wrap
+    // or bounce in y.
+    const bool x_inner = x0 > 0 && x0 + SW < nx;
     const T c3 = T(1.0 / 3.0), c6 = T(0.5 / 3.0);
+
     for (int y = yfirst; y < ye; ++y) {
         cp_async_wait<DEPTH - 1>();   // row y+3 has landed (this thread's chunks)
-        __syncthreads();              // ... everyone's; and row y-1 is free
-        issue_row(y + 3 + DEPTH);     // into the buffer of row y-1
+        __syncthreads();              // ... everyone's; and row y-1's buffer is free
+        issue_row(y + 3 + DEPTH);
 
         // 1. phi at row y+3, columns -3 .. SW+2
         {
             const char *b = s.buf(y + 3);
             T *ph = s.phir(y + 3);
-            for (int c = t - 3; c < SW + 3; c += SW) {
+            columns<SW, 3, 3>(t, [&](int c) {
                 T g[9];
-                SR::template read_g<LW>(b, c + HP, g);
-                T a = g[0];
-#pragma unroll
-                for (int i = 1; i < 9; ++i) a += g[i];
-                ph[c] = a;
-            }
+                SR::read_g(b, c + HP, g);
+                ph[c] = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+            });
         }
         // 2. sum f and j at row y+1, columns -1 .. SW
         {
             const char *b = s.buf(y + 1);
-            for (int c = t - 1; c < SW + 1; c += SW) {
+            columns<SW, 1, 2>(t, [&](int c) {
                 T f[9];
-                SR::template read_f<LW>(b, c + HP, f);
-                T a = f[0];
-#pragma unroll
-                for (int i = 1; i < 9; ++i) a += f[i];
-                s.ps[c + 1] = a;
+                SR::read_f(b, c + HP, f);
+                s.ps[c + 1] = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
                 s.jx[c + 1] = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
                 s.jy[c + 1] = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
-            }
+            });
         }
         __syncthreads();
 
@@ -248,18 +319,19 @@ k_strip(const char *__restrict__ src, char *__restrict__ dst, const KP<T> P, int
             if (!ghost) {
                 const T *pu = s.phir(r + 1), *pc = s.phir(r), *pd = s.phir(r - 1);
                 T *mlow = (wall && r == 0) ? s.mur(-1) : nullptr;
-                for (int c = t - 2; c < SW + 2; c += SW) {
+                columns<SW, 2, 1>(t, [&](int c) {
                     const T C = pc[c];
-                    const T ax = (pc[c + 1] - C) + (pc[c - 1] - C) + (pu[c] - C) + (pd[c] - C);
-                    const T dg = (pu[c + 1] - C) + (pu[c - 1] - C) + (pd[c - 1] - C) + (pd[c + 1] - C);
-                    const T lap = T(6) * (ax * T(1.0 / 9.0) + dg * T(1.0 / 36.0));
+                    // lap = (2/cs2) sum w_i (phi(x + c_i) - phi(x)), differences first
+                    const T ax = ((pc[c + 1] - C) + (pc[c - 1] - C)) + ((pu[c] - C) + (pd[c] - C));
+                    const T dg = ((pu[c + 1] - C) + (pu[c - 1] - C)) + ((pd[c - 1] - C) + (pd[c + 1] - C));
+                    const T lap = T(2.0 / 3.0) * ax + T(1.0 / 6.0) * dg;
                     const T m = P.beta4 * (C - P.phiA) * (C - P.phiB) * (C - P.phibar) - P.kappa * lap;
                     mo[c] = m;
                     if (mlow) mlow[c] = m;  // ghost row -1 mirrors row 0
-                }
+                });
             } else if (r >= ny) {
                 const T *mm = s.mur(2 * ny - 1 - r);  // mirror row (already computed)
-                for (int c = t - 2; c < SW + 2; c += SW) mo[c] = mm[c];
+                columns<SW, 2, 1>(t, [&](int c) { mo[c] = mm[c]; });
             }
             // r < 0 at a wall: row -1 is written when row 0 is computed;
             // rows below are never read.
@@ -274,24 +346,24 @@ k_strip(const char *__restrict__ src, char *__restrict__ dst, const KP<T> P, int
             if (!wall || (r >= 0 && r < ny)) {
                 const T *pu = s.phir(r + 1), *pc = s.phir(r), *pd = s.phir(r - 1);
                 const T *mu_ = s.mur(r + 1), *mc = s.mur(r), *md = s.mur(r - 1);
-                for (int c = t - 1; c < SW + 1; c += SW) {
+                columns<SW, 1, 0>(t, [&](int c) {
                     const T phi = pc[c];
-                    const T gphx = T(3) * ((pc[c + 1] - pc[c - 1]) * T(1.0 / 9.0) +
-                                           ((pu[c + 1] - pu[c - 1]) + (pd[c + 1] - pd[c - 1])) * T(1.0 / 36.0));
-                    const T gphy = T(3) * ((pu[c] - pd[c]) * T(1.0 / 9.0) +
-                                           ((pu[c + 1] + pu[c - 1]) - (pd[c - 1] + pd[c + 1])) * T(1.0 / 36.0));
+                    const T pul = pu[c - 1], pur = pu[c + 1], pdl = pd[c - 1], pdr = pd[c + 1];
+                    const T gphx = T(1.0 / 3.0) * (pc[c + 1] - pc[c - 1]) +
+                                   T(1.0 / 12.0) * ((pur - pul) + (pdr - pdl));
+                    const T gphy = T(1.0 / 3.0) * (pu[c] - pd[c]) +
+                                   T(1.0 / 12.0) * ((pur + pul) - (pdl + pdr));
                     const T M = mc[c];
-                    const T gmx = T(3) * ((mc[c + 1] - mc[c - 1]) * T(1.0 / 9.0) +
-                                          ((mu_[c + 1] - mu_[c - 1]) + (md[c + 1] - md[c - 1])) * T(1.0 / 36.0));
-                    const T gmy = T(3) * ((mu_[c] - md[c]) * T(1.0 / 9.0) +
-                                          ((mu_[c + 1] + mu_[c - 1]) - (md[c - 1] + md[c + 1])) * T(1.0 / 36.0));
-                    const T ax = (mc[c + 1] - M) + (mc[c - 1] - M) + (mu_[c] - M) + (md[c] - M);
-                    const T dg = (mu_[c + 1] - M) + (mu_[c - 1] - M) + (md[c - 1] - M) + (md[c + 1] - M);
-                    const T lm = T(6) * (ax * T(1.0 / 9.0) + dg * T(1.0 / 36.0));
+                    const T mul = mu_[c - 1], mur_ = mu_[c + 1], mdl = md[c - 1], mdr = md[c + 1];
+                    const T mcl = mc[c - 1], mcr = mc[c + 1], mcu = mu_[c], mcd = md[c];
+                    const T gmx = T(1.0 / 3.0) * (mcr - mcl) + T(1.0 / 12.0) * ((mur_ - mul) + (mdr - mdl));
+                    const T gmy = T(1.0 / 3.0) * (mcu - mcd) + T(1.0 / 12.0) * ((mur_ + mul) - (mdl + mdr));
+                    const T lm = T(2.0 / 3.0) * (((mcl - M) + (mcr - M)) + ((mcu - M) + (mcd - M))) +
+                                 T(1.0 / 6.0) * (((mur_ - M) + (mul - M)) + ((mdl - M) + (mdr - M)));
                     const T rho = P.rhoB + (phi - P.phiB) * P.drho;
                     const T Fx = -phi * gmx;
                     const T Fy = -phi * gmy - (rho - P.rhoref) * P.grav;
-                    const T irc = T(3) / rho;
+                    const T irc = T(3) * rcp_fast(rho);
                     const T ux = (s.jx[c + 1] + c6 * Fx) * irc;
                     const T uy = (s.jy[c + 1] + c6 * Fy) * irc;
                     const T udr = (ux * gphx + uy * gphy) * P.drho;
@@ -301,13 +373,13 @@ k_strip(const char *__restrict__ src, char *__restrict__ dst, const KP<T> P, int
                     s.Fx[uo + c] = Fx;
                     s.Fy[uo + c] = Fy;
                     s.lmu[uo + c] = lm;
-                    s.gpx_[uo + c] = gphx;
-                    s.gpy_[uo + c] = gphy;
-                }
+                    s.gphx[uo + c] = gphx;
+                    s.gphy[uo + c] = gphy;
+                });
             } else if (r == ny) {
                 // ghost row above the top wall: linear extrapolation of p
                 const T *p1 = s.pr(ny - 1), *p2 = s.pr(ny - 2);
-                for (int c = t - 1; c < SW + 1; c += SW) po[c] = T(2) * p1[c] - p2[c];
+                columns<SW, 1, 0>(t, [&](int c) { po[c] = T(2) * p1[c] - p2[c]; });
             }
         }
         __syncthreads();
@@ -318,16 +390,15 @@ k_strip(const char *__restrict__ src, char *__restrict__ dst, const KP<T> P, int
             const int gx = x0 + c;
             if (gx < nx) {
                 const int uo = s.ur(y);
-                const T *pc = s.pr(y), *pu = s.pr(y + 1);
-                const T *pd = s.pr(y - 1);
+                const T *pc = s.pr(y), *pu = s.pr(y + 1), *pd = s.pr(y - 1);
                 const bool lowghost = wall && y == 0;
-                T pdm = lowghost ? T(2) * pc[c - 1] - pu[c - 1] : pd[c - 1];
-                T pd0 = lowghost ? T(2) * pc[c] - pu[c] : pd[c];
-                T pdp = lowghost ? T(2) * pc[c + 1] - pu[c + 1] : pd[c + 1];
-                const T gpx = T(3) * ((pc[c + 1] - pc[c - 1]) * T(1.0 / 9.0) +
-                                      ((pu[c + 1] - pu[c - 1]) + (pdp - pdm)) * T(1.0 / 36.0));
-                const T gpy = T(3) * ((pu[c] - pd0) * T(1.0 / 9.0) +
-                                      ((pu[c + 1] + pu[c - 1]) - (pdm + pdp)) * T(1.0 / 36.0));
+                const T pdm = lowghost ? T(2) * pc[c - 1] - pu[c - 1] : pd[c - 1];
+                const T pd0 = lowghost ? T(2) * pc[c] - pu[c] : pd[c];
+                const T pdp = lowghost ? T(2) * pc[c + 1] - pu[c + 1] : pd[c + 1];
+                const T gpx = T(1.0 / 3.0) * (pc[c + 1] - pc[c - 1]) +
+                              T(1.0 / 12.0) * ((pu[c + 1] - pu[c - 1]) + (pdp - pdm));
+                const T gpy = T(1.0 / 3.0) * (pu[c] - pd0) +
+                              T(1.0 / 12.0) * ((pu[c + 1] + pu[c - 1]) - (pdm + pdp));
                 const T phi = s.phir(y)[c];
                 const T mu = s.mur(y)[c];
                 const T pv = pc[c];
@@ -335,58 +406,73 @@ k_strip(const char *__restrict__ src, char *__restrict__ dst, const KP<T> P, int
                 const T Fx = s.Fx[uo + c], Fy = s.Fy[uo + c];
                 const T lm = s.lmu[uo + c];
                 const T rho = P.rhoB + (phi - P.phiB) * P.drho;
-                const T grx = P.drho * s.gpx_[uo + c], gry = P.drho * s.gpy_[uo + c];
+                const T gr3x = (c3 * P.drho) * s.gphx[uo + c];   // grad rho / 3
+                const T gr3y = (c3 * P.drho) * s.gphy[uo + c];
                 T f[9], g[9];
                 const char *b = s.buf(y);
-                SR::template read_f<LW>(b, c + HP, f);
-                SR::template read_g<LW>(b, c + HP, g);
+                SR::read_f(b, c + HP, f);
+                SR::read_g(b, c + HP, g);
 
-                const T uu = ux * ux + uy * uy;
-                const T amu = P.alpha * mu;
-                const T srcF = c3 * rho * P.gl * lm;
-                const T gq = -T(3) * phi / rho;
+                // per-cell terms (see the collision below)
+                const T uu15 = T(1.5) * (ux * ux + uy * uy);
+                const T irho = rcp_fast(rho);
+                const T Q = P.pg * (T(-3) * phi * irho);           // pg * (-phi / (cs2 rho))
                 const T dx = gpx - Fx, dy = gpy - Fy;
-                const T uF = ux * Fx + uy * Fy, uR = ux * grx + uy * gry, uD = ux * dx + uy * dy;
-                const T rho3 = c3 * rho;
+                const T uF = ux * Fx + uy * Fy;
+                const T uR3 = ux * gr3x + uy * gr3y;
+                const T uD = ux * dx + uy * dy;
+                const T Bf = P.itf * (c3 * rho);                    // itf cs2 rho
+                const T Kf = P.itf * pv - P.pf * (c3 * rho * P.gl * lm);
+                const T omf = T(1) - P.itf, omg = T(1) - P.itg;
+                const T phg = P.itg * phi;
+                const T Ag = P.itg * P.alpha * mu;                  // itg alpha mu
                 T fv[9], gv[9];
-                int sl[9];
-                long long kk[9];
-                const long long k = (long long)y * nx + gx;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     const int cx = D2Q9::cx(i), cy = D2Q9::cy(i);
                     const T w = T(D2Q9::w(i));
                     const T cu = T(cx) * ux + T(cy) * uy;
-                    const T si = cu * (T(3) + T(4.5) * cu) - T(1.5) * uu;
-                    const T eF = (T(cx) * Fx + T(cy) * Fy) - uF;
-                    const T eR = (T(cx) * grx + T(cy) * gry) - uR;
-                    const T eD = (T(cx) * dx + T(cy) * dy) - uD;
-                    const T G1 = T(1) + si;
-                    const T Fi = w * (G1 * eF + (si * c3) * eR - srcF);
-                    const T Gi = w * gq * G1 * eD;
-                    const T feq = w * (pv + rho3 * si);
-                    const T H = (i == 0) ? phi - T(1.0 - D2Q9::w(0)) * amu : w * amu;
-                    const T geq = H + w * phi * si;
-                    T fs = f[i] - (f[i] - feq) * P.itf + P.pf * Fi;
-                    T gs = g[i] - (g[i] - geq) * P.itg + P.pg * Gi;
-                    const int yd = y + cy;
-                    if (wall && (yd < 0 || yd >= ny)) {
-                        const T cuw = T(cx) * (yd < 0 ? P.uwb : P.uwt);
-                        fs -= T(2) * w * rho * cuw;
-                        gs -= T(6) * w * phi * cuw;
-                        sl[i] = D2Q9::opp(i);
-                        kk[i] = k;
-                    } else {
-                        int xd = gx + cx;
-                        xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
-                        const int yy = yd < 0 ? yd + ny : (yd >= ny ? yd - ny : yd);
-                        sl[i] = i;
-                        kk[i] = (long long)yy * nx + xd;
-                    }
-                    fv[i] = fs;
-                    gv[i] = gs;
+                    const T si = cu * (T(3) + T(4.5) * cu) - uu15;   // s_i (Eq. 26)
+                    const T eF = (T(cx) * Fx + T(cy) * Fy) - uF;       // (c_i - u).F
+                    const T eR = (T(cx) * gr3x + T(cy) * gr3y) - uR3;  // (c_i - u).grad rho / 3
+                    const T eD = (T(cx) * dx + T(cy) * dy) - uD;       // (c_i - u).(grad p - F)
+                    // f* = f - (f - f^eq)/tau_f + (1 - 1/2tau_f) F_i  (Eqs. 22, 24, 28)
+                    const T t1 = eF + si * (eF + eR);
+                    fv[i] = omf * f[i] + w * (Kf + Bf * si + P.pf * t1);
+                    // g* = g - (g - g^eq)/tau_g + (1 - 1/2tau_g) G_i  (Eqs. 23, 25, 27, 29)
+                    const T t2 = eD + si * eD;
+                    const T Hg = (i == 0) ? (phg - T(1.0 - D2Q9::w(0)) * Ag) * T(1.0 / D2Q9::w(0))
+                                          : Ag;
+                    gv[i] = omg * g[i] + w * (Hg + phg * si + Q * t2);
                 }
-                ST::store(dst, NS, sl, kk, fv, gv, phi);
+                const bool y_inner = y > 0 && y < ny - 1;
+                if (x_inner && y_inner) {
+                    SR::store_fast(dst, NS, nx, y * nx + gx, fv, gv, phi);
+                } else {
+                    int sl[9];
+                    long long kk[9];
+                    const long long k = (long long)y * nx + gx;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const int cx = D2Q9::cx(i), cy = D2Q9::cy(i);
+                        const int yd = y + cy;
+                        if (wall && (yd < 0 || yd >= ny)) {
+                            const T w = T(D2Q9::w(i));
+                            const T cuw = T(cx) * (yd < 0 ? P.uwb : P.uwt);
+                            fv[i] -= T(2) * w * rho * cuw;
+                            gv[i] -= T(6) * w * phi * cuw;
+                            sl[i] = D2Q9::opp(i);
+                            kk[i] = k;
+                        } else {
+                            int xd = gx + cx;
+                            xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
+                            const int yy = yd < 0 ? yd + ny : (yd >= ny ? yd - ny : yd);
+                            sl[i] = i;
+                            kk[i] = (long long)yy * nx + xd;
+                        }
+                    }
+                    ST::store(dst, P.NS, sl, kk, fv, gv, phi);
+                }
             }
         }
     }

@@ -116,7 +116,9 @@ def test_f64_populations_match_oracle(lbm):
 
 def _window_check(L, p, phi, dtype, steps, samples, tol_phi_u, rel64=None):
     """Full-size GPU run checked at sampled cells against the oracle on a
-    periodic window (half-width h > 4 steps + 1) around each sample."""
+    periodic window (half-width h > 4 steps + 1) around each sample.  FP64:
+    max error over the samples within rel64 of the largest sampled oracle
+    magnitude of that field; FP32: max-abs bound on phi and u."""
     ny, nx = phi.shape
     s = L.Sim(p, dtype)
     s.init_phi(phi)
@@ -124,6 +126,8 @@ def _window_check(L, p, phi, dtype, steps, samples, tol_phi_u, rel64=None):
     g = {k: v.double().cpu().numpy() for k, v in s.fields().items()}
     s.close()
     h = 4 * steps + 1 + 8
+    got = {k: [] for k in ("phi", "ux", "uy", "p")}
+    ref = {k: [] for k in got}
     for (yy, xx) in samples:
         ys = np.arange(yy - h, yy + h + 1) % ny
         xs = np.arange(xx - h, xx + h + 1) % nx
@@ -133,12 +137,16 @@ def _window_check(L, p, phi, dtype, steps, samples, tol_phi_u, rel64=None):
         o.init_phi(win)
         o.step(steps)
         of = o.fields()
-        for k in ("phi", "ux", "uy", "p"):
-            a, b = g[k][yy, xx], of[k][h, h]
-            if rel64 is not None:
-                assert abs(a - b) <= rel64 * max(abs(b), 1e-3 if k == "phi" else 1e-6), (k, yy, xx, a, b)
-            elif k in ("phi", "ux", "uy"):
-                assert abs(a - b) <= tol_phi_u, (k, yy, xx, a, b)
+        for k in got:
+            got[k].append(g[k][yy, xx])
+            ref[k].append(of[k][h, h])
+    for k in got:
+        a, b = np.array(got[k]), np.array(ref[k])
+        err = np.abs(a - b).max()
+        if rel64 is not None:
+            assert err <= rel64 * np.abs(b).max(), (k, err, np.abs(b).max())
+        elif k in ("phi", "ux", "uy"):
+            assert err <= tol_phi_u, (k, err)
 
 
 def _samples(nx, ny, seed, n=12):
