@@ -2,5 +2,5 @@
 #include "lbm_ops.cuh"
 
 namespace lbm {
-const Ops *ops_f32() { return OpsImpl<float, PlainStore<float>, 2, 128, 2>::ops("f32"); }
+const Ops *ops_f32() { return OpsImpl<float, PlainStore<float>, 2, 128, 1>::ops("f32"); }
 }  // namespace lbm

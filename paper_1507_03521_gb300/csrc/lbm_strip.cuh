@@ -67,16 +67,20 @@ struct StripRow<PlainStore<T>, SW> {
     static constexpr int LW = SW + 2 * HP;     // row width
     static constexpr int CE = 16 / sizeof(T);  // elements per 16-byte chunk
     static constexpr int CPS = LW / CE;        // chunks per slot
-    static constexpr int TOTAL = 18 * CPS;
+    static constexpr int TOTAL = 9 * CPS;      // chunks of one f row (or g row)
     static constexpr int NCH = (TOTAL + SW - 1) / SW;
-    static constexpr size_t bytes = (size_t)18 * LW * sizeof(T);
+    static constexpr size_t fbytes = (size_t)9 * LW * sizeof(T);  // f_0..f_8
+    static constexpr size_t gbytes = (size_t)9 * LW * sizeof(T);  // g_0..g_8
     static bool idx32_ok(long long NS) { return 18 * NS < (1LL << 31); }
 
+    // A thread copies the same chunks of every f row and of every g row.
     struct Desc {
         int goff[NCH], soff[NCH];
+        int gslot;  // element offset of the g slots: 9 NS
     };
     __device__ __forceinline__ static void describe(Desc &d, int t, long long NS, int x_start,
                                                     int nx) {
+        d.gslot = 9 * (int)NS;
 #pragma unroll
         for (int k = 0; k < NCH; ++k) {
             const int j = t + k * SW;
@@ -90,23 +94,31 @@ struct StripRow<PlainStore<T>, SW> {
             }
         }
     }
-    __device__ __forceinline__ static void issue(const Desc &d, char *sbuf, const char *lvl,
-                                                 int rowbase) {
+    __device__ __forceinline__ static void issue_f(const Desc &d, char *sbuf, const char *lvl,
+                                                   int rowbase) {
         const T *g = reinterpret_cast<const T *>(lvl);
         T *s = reinterpret_cast<T *>(sbuf);
 #pragma unroll
         for (int k = 0; k < NCH; ++k)
             if (d.goff[k] >= 0) cp_async16(s + d.soff[k], g + (d.goff[k] + rowbase));
     }
-    __device__ __forceinline__ static void read_f(const char *sbuf, int c, C f[9]) {
-        const T *s = reinterpret_cast<const T *>(sbuf);
+    __device__ __forceinline__ static void issue_g(const Desc &d, char *sbuf, const char *lvl,
+                                                   int rowbase) {
+        const T *g = reinterpret_cast<const T *>(lvl) + d.gslot;
+        T *s = reinterpret_cast<T *>(sbuf);
+#pragma unroll
+        for (int k = 0; k < NCH; ++k)
+            if (d.goff[k] >= 0) cp_async16(s + d.soff[k], g + (d.goff[k] + rowbase));
+    }
+    __device__ __forceinline__ static void read_f(const char *fbuf, int c, C f[9]) {
+        const T *s = reinterpret_cast<const T *>(fbuf);
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = s[i * LW + c];
     }
-    __device__ __forceinline__ static void read_g(const char *sbuf, int c, C g[9]) {
-        const T *s = reinterpret_cast<const T *>(sbuf);
+    __device__ __forceinline__ static void read_g(const char *gbuf, int c, C g[9]) {
+        const T *s = reinterpret_cast<const T *>(gbuf);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = s[(9 + i) * LW + c];
+        for (int i = 0; i < 9; ++i) g[i] = s[i * LW + c];
     }
     // Interior push: slot i of cell kb + cy_i nx + cx_i, 32-bit offsets.
     __device__ __forceinline__ static void store_fast(char *lvl, int NS, int nx, int kb,
@@ -125,61 +137,86 @@ struct StripRow<Store16<H>, SW> {
     using E = HalfStore<H>;
     static constexpr int HP = 8;  // 8 halves per 16-byte chunk
     static constexpr int LW = SW + 2 * HP;
-    static constexpr int C0 = LW / 4, CH = LW / 8;  // chunks: g0 row (floats), each half slot
-    static constexpr int N0 = (C0 + SW - 1) / SW, NH = (17 * CH + SW - 1) / SW;
-    static constexpr size_t bytes = (size_t)LW * 4 + (size_t)17 * LW * 2;
-    // half offsets are counted from the level base: the half slots start at
-    // half index 2 NS (after NS floats of g_0)
+    static constexpr int CH = LW / 8, C0 = LW / 4;  // chunks per half slot, of the g_0 row
+    static constexpr int TF = 9 * CH;               // f row: half slots 0..8
+    static constexpr int TG = C0 + 8 * CH;          // g row: g_0 floats, half slots 9..16
+    static constexpr int NF = (TF + SW - 1) / SW, NG = (TG + SW - 1) / SW;
+    static constexpr size_t fbytes = (size_t)9 * LW * 2;
+    static constexpr size_t gbytes = (size_t)LW * 4 + (size_t)8 * LW * 2;
+    // offsets count halves from the level base: half slot s starts at half
+    // index (2 + s) NS, after the NS floats of g_0
     static bool idx32_ok(long long NS) { return 19 * NS < (1LL << 31); }
 
     struct Desc {
-        int g0off[N0], s0off[N0], hoff[NH], shoff[NH];
+        int foff[NF], fso[NF];      // f chunks: global half offset, smem half offset
+        int goff[NG], gso[NG];      // g chunks: global offset (floats for g_0, else halves)
+        unsigned gflt;              // bit k: chunk k of the g row is a g_0 (float) chunk
     };
     __device__ __forceinline__ static void describe(Desc &d, int t, long long NS, int x_start,
                                                     int nx) {
+        const int ns = (int)NS;
 #pragma unroll
-        for (int k = 0; k < N0; ++k) {
+        for (int k = 0; k < NF; ++k) {
             const int j = t + k * SW;
-            d.g0off[k] = j < C0 ? wrap_any(x_start + j * 4, nx) : -1;
-            d.s0off[k] = j * 4;
-        }
-#pragma unroll
-        for (int k = 0; k < NH; ++k) {
-            const int j = t + k * SW;
-            if (j < 17 * CH) {
+            if (j < TF) {
                 const int sl = j / CH, c = j - sl * CH;
-                d.hoff[k] = (2 + sl) * (int)NS + wrap_any(x_start + c * 8, nx);
-                d.shoff[k] = sl * LW + c * 8;
+                d.foff[k] = (2 + sl) * ns + wrap_any(x_start + c * 8, nx);
+                d.fso[k] = sl * LW + c * 8;
             } else {
-                d.hoff[k] = -1;
-                d.shoff[k] = 0;
+                d.foff[k] = -1;
+                d.fso[k] = 0;
+            }
+        }
+        d.gflt = 0;
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+            const int j = t + k * SW;
+            if (j < C0) {
+                d.goff[k] = wrap_any(x_start + j * 4, nx);
+                d.gso[k] = j * 16;  // bytes
+                d.gflt |= 1u << k;
+            } else if (j < TG) {
+                const int jj = j - C0;
+                const int sl = jj / CH, c = jj - sl * CH;
+                d.goff[k] = (2 + 9 + sl) * ns + wrap_any(x_start + c * 8, nx);
+                d.gso[k] = LW * 4 + (sl * LW + c * 8) * 2;  // bytes
+            } else {
+                d.goff[k] = -1;
+                d.gso[k] = 0;
             }
         }
     }
-    __device__ __forceinline__ static void issue(const Desc &d, char *sbuf, const char *lvl,
-                                                 int rowbase) {
+    __device__ __forceinline__ static void issue_f(const Desc &d, char *sbuf, const char *lvl,
+                                                   int rowbase) {
+        const unsigned short *h = reinterpret_cast<const unsigned short *>(lvl);
+        unsigned short *sh = reinterpret_cast<unsigned short *>(sbuf);
+#pragma unroll
+        for (int k = 0; k < NF; ++k)
+            if (d.foff[k] >= 0) cp_async16(sh + d.fso[k], h + (d.foff[k] + rowbase));
+    }
+    __device__ __forceinline__ static void issue_g(const Desc &d, char *sbuf, const char *lvl,
+                                                   int rowbase) {
         const float *g0 = reinterpret_cast<const float *>(lvl);
         const unsigned short *h = reinterpret_cast<const unsigned short *>(lvl);
-        float *s0 = reinterpret_cast<float *>(sbuf);
-        unsigned short *sh = reinterpret_cast<unsigned short *>(sbuf + (size_t)LW * 4);
 #pragma unroll
-        for (int k = 0; k < N0; ++k)
-            if (d.g0off[k] >= 0) cp_async16(s0 + d.s0off[k], g0 + (d.g0off[k] + rowbase));
-#pragma unroll
-        for (int k = 0; k < NH; ++k)
-            if (d.hoff[k] >= 0) cp_async16(sh + d.shoff[k], h + (d.hoff[k] + rowbase));
+        for (int k = 0; k < NG; ++k) {
+            if (d.goff[k] < 0) continue;
+            const void *src = ((d.gflt >> k) & 1u) ? static_cast<const void *>(g0 + (d.goff[k] + rowbase))
+                                                   : static_cast<const void *>(h + (d.goff[k] + rowbase));
+            cp_async16(sbuf + d.gso[k], src);
+        }
     }
-    __device__ __forceinline__ static void read_f(const char *sbuf, int c, C f[9]) {
-        const unsigned short *sh = reinterpret_cast<const unsigned short *>(sbuf + (size_t)LW * 4);
+    __device__ __forceinline__ static void read_f(const char *fbuf, int c, C f[9]) {
+        const unsigned short *sh = reinterpret_cast<const unsigned short *>(fbuf);
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = E::dec(sh[i * LW + c]);
     }
-    __device__ __forceinline__ static void read_g(const char *sbuf, int c, C g[9]) {
-        const float *s0 = reinterpret_cast<const float *>(sbuf);
-        const unsigned short *sh = reinterpret_cast<const unsigned short *>(sbuf + (size_t)LW * 4);
+    __device__ __forceinline__ static void read_g(const char *gbuf, int c, C g[9]) {
+        const float *s0 = reinterpret_cast<const float *>(gbuf);
+        const unsigned short *sh = reinterpret_cast<const unsigned short *>(gbuf + (size_t)LW * 4);
         g[0] = s0[c];
 #pragma unroll
-        for (int i = 1; i < 9; ++i) g[i] = E::dec(sh[(8 + i) * LW + c]);
+        for (int i = 1; i < 9; ++i) g[i] = E::dec(sh[(i - 1) * LW + c]);
     }
     __device__ __forceinline__ static void store_fast(char *lvl, int NS, int nx, int kb,
                                                       const C fv[9], const C gv[9], C phi) {
@@ -204,11 +241,14 @@ struct StripSmem {
     using SR = StripRow<ST, SW>;
     static constexpr int HP = SR::HP;
     static constexpr int LW = SR::LW;
-    static constexpr int NB = DEPTH + 4;       // population row buffers
+    // g rows are read 3 iterations after they arrive (phi, then collision),
+    // f rows 1 iteration after (sum f and j, then collision): separate rings.
+    static constexpr int NBG = DEPTH + 4, NBF = DEPTH + 2;
     static constexpr int RPHI = 5, RMU = 4, RP = 3, RU = 2;
     static constexpr int WPHI = SW + 6, WMU = SW + 4, WQ = SW + 2;
-    static constexpr size_t popb = (SR::bytes + 15) / 16 * 16;
-    static constexpr size_t pop_bytes = popb * NB;
+    static constexpr size_t gb = (SR::gbytes + 15) / 16 * 16;
+    static constexpr size_t fb = (SR::fbytes + 15) / 16 * 16;
+    static constexpr size_t pop_bytes = gb * NBG + fb * NBF;
     // fields: phi ring, mu ring, p ring, ps/jx/jy (1 row), and a 2-row ring
     // of ux, uy, Fx, Fy, lap mu, grad phi (x, y)
     static constexpr size_t fld_elems =
@@ -233,7 +273,10 @@ struct StripSmem {
         gphx = lmu + RU * WQ;
         gphy = gphx + RU * WQ;
     }
-    __device__ __forceinline__ char *buf(int row) const { return pop + (size_t)((row + 64) % NB) * popb; }
+    __device__ __forceinline__ char *gbuf(int row) const { return pop + (size_t)((row + 64) % NBG) * gb; }
+    __device__ __forceinline__ char *fbuf(int row) const {
+        return pop + gb * NBG + (size_t)((row + 64) % NBF) * fb;
+    }
     // ring row pointers; column index relative to the strip's first column
     __device__ __forceinline__ T *phir(int row) const { return phi + ((row + 64) % RPHI) * WPHI + 3; }
     __device__ __forceinline__ T *mur(int row) const { return mu + ((row + 64) % RMU) * WMU + 2; }
@@ -271,12 +314,16 @@ k_strip(const char *__restrict__ src, char *__restrict__ dst, const KP<T> P, int
     SR::describe(desc, t, P.NS, x0 - HP, nx);
     __syncthreads();
 
-    auto issue_row = [&](int row) {
-        if (row <= ye + 2) SR::issue(desc, s.buf(row), src, src_row(row, ny, wall) * nx);
-        cp_async_commit();  // one group per row, possibly empty
+    // Iteration y reads g row y+3 and f row y+1 first; both are issued
+    // DEPTH iterations earlier, as one commit group.
+    auto issue_for = [&](int it) {
+        const int gr = it + 3, fr = it + 1;
+        if (gr <= ye + 2) SR::issue_g(desc, s.gbuf(gr), src, src_row(gr, ny, wall) * nx);
+        if (fr <= ye) SR::issue_f(desc, s.fbuf(fr), src, src_row(fr, ny, wall) * nx);
+        cp_async_commit();  // one group per iteration, possibly empty
     };
 #pragma unroll
-    for (int d = 0; d < DEPTH; ++d) issue_row(yfirst + 3 + d);
+    for (int d = 0; d < DEPTH; ++d) issue_for(yfirst + d);
 
     // Interior strips never wrap in x when pushing; interior rows never wrap
     // or bounce in y.
@@ -284,13 +331,13 @@ k_strip(const char *__restrict__ src, char *__restrict__ dst, const KP<T> P, int
     const T c3 = T(1.0 / 3.0), c6 = T(0.5 / 3.0);
 
     for (int y = yfirst; y < ye; ++y) {
-        cp_async_wait<DEPTH - 1>();   // row y+3 has landed (this thread's chunks)
-        __syncthreads();              // ... everyone's; and row y-1's buffer is free
-        issue_row(y + 3 + DEPTH);
+        cp_async_wait<DEPTH - 1>();   // g row y+3, f row y+1 have landed (own chunks)
+        __syncthreads();              // ... everyone's; rows y-1 are free
+        issue_for(y + DEPTH);         // into the buffers of g row y-1, f row y-1
 
         // 1. phi at row y+3, columns -3 .. SW+2
         {
-            const char *b = s.buf(y + 3);
+            const char *b = s.gbuf(y + 3);
             T *ph = s.phir(y + 3);
             columns<SW, 3, 3>(t, [&](int c) {
                 T g[9];
@@ -300,7 +347,7 @@ k_strip(const char *__restrict__ src, char *__restrict__ dst, const KP<T> P, int
         }
         // 2. sum f and j at row y+1, columns -1 .. SW
         {
-            const char *b = s.buf(y + 1);
+            const char *b = s.fbuf(y + 1);
             columns<SW, 1, 2>(t, [&](int c) {
                 T f[9];
                 SR::read_f(b, c + HP, f);
@@ -409,9 +456,8 @@ k_strip(const char *__restrict__ src, char *__restrict__ dst, const KP<T> P, int
                 const T gr3x = (c3 * P.drho) * s.gphx[uo + c];   // grad rho / 3
                 const T gr3y = (c3 * P.drho) * s.gphy[uo + c];
                 T f[9], g[9];
-                const char *b = s.buf(y);
-                SR::read_f(b, c + HP, f);
-                SR::read_g(b, c + HP, g);
+                SR::read_f(s.fbuf(y), c + HP, f);
+                SR::read_g(s.gbuf(y), c + HP, g);
 
                 // per-cell terms (see the collision below)
                 const T uu15 = T(1.5) * (ux * ux + uy * uy);
