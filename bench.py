@@ -266,7 +266,10 @@ def main():
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": _traffic("f32"), "peak_kind": peak_kind,
-                         "bytes_per_cell": BYTES_PER_CELL["f32"], "kernel": "k_step<float>"},
+                         "bytes_per_cell": BYTES_PER_CELL["f32"],
+                         "kernel": "k_strip<float>" if n % 8 == 0 else "k_step<float>",
+                         "launch_ms": {"mean": round(avg_launch_ms, 5), "min": round(min(per), 5),
+                                       "max": round(max(per), 5)}},
             "gpu_launches": args.steps, "clocks": ck}
 
     if not args.no_forms:
@@ -279,7 +282,7 @@ def main():
             ach2 = BYTES_PER_CELL[dtype] * cells / (statistics.mean(per2) * 1e-3) / 1e9
             forms[dtype] = {"mlups": round(m2, 2), "ms_per_step": round(tot / ksteps, 5),
                             "hbm_gbs": round(ach2, 1), "frac": round(ach2 / peak, 4),
-                            "bytes_per_cell": BYTES_PER_CELL[dtype]}
+                            "bytes_per_cell": BYTES_PER_CELL[dtype], "traffic": _traffic(dtype)}
             s2.close()
         # errors after the same number of steps, against the FP64 path
         errs = {}
