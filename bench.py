@@ -190,6 +190,44 @@ def run_reference(args, rank, world):
     return 0
 
 
+def measure_batch(lbm, W, args, peak, dist):
+    """Batched workload: 1024 periodic domains, sides uniform in
+    {64, 96, ..., 512}, droplet or layer, rho ratio log-uniform in [1, 100],
+    sigma U[1e-4, 1e-2], M U[0.01, 0.2]; FP32, one launch per step replayed
+    from a CUDA graph, segment height autotuned."""
+    import torch
+    doms = W.batch_domains(1024, seed=1507036)
+    b = lbm.Batch([p for p, _ in doms], "f32", graph=True)
+    phis = [phi for _, phi in doms]
+    b.init_phi(phis)
+    seg, _ = b.autotune(steps=3)
+    b.init_phi(phis)
+    b.step(args.warmup)
+    st = b.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0.record(st)
+    b.step(args.steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cells = b.cells
+    world = dist.get_world_size() if dist is not None else 1
+    gbs = BYTES_PER_CELL["f32"] * cells / (ms / args.steps * 1e-3) / 1e9
+    b.close()
+    return {"workload": "batch-1024-domains-64to512", "domains": 1024, "cells": cells,
+            "mlups": round(cells * args.steps * world / (ms * 1e-3) / 1e6, 2),
+            "ms_per_step": round(ms / args.steps, 5), "hbm_gbs": round(gbs, 1),
+            "frac": round(gbs / peak, 4), "seg_h": seg, "graph": True,
+            "launches_per_step": 1, "kernel": "k_strip_batch<float>"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -199,6 +237,7 @@ def main():
     ap.add_argument("--n", type=int, default=4096, help="grid side (default: the workload's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the f16s/bf16s/f64 forms")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -305,6 +344,9 @@ def main():
             forms[dtype]["steps_for_err"] = K
         forms["f32"] = {"max_abs_err_vs_f64": errs["f32"], "steps_for_err": K}
         line["forms"] = forms
+
+    if not args.no_batch:
+        line["batched"] = measure_batch(lbm, W, args, peak, dist)
 
     # End to end through the C ABI with host buffers: phi0 in, K steps,
     # phi/u/p out and the mass diagnostic, all inside the timed region.

@@ -163,12 +163,64 @@ LBM_API int64_t lbm_step_count(const lbm_sim *sim);
  * call on the handle. */
 LBM_API const char *lbm_last_error(const lbm_sim *sim);
 
-/* Message of the last lbm_create / lbm_buffer_sizes / lbm_mass_noalloc
- * failure in this thread (those calls have no handle to store it in). */
+/* Message of the last lbm_create / lbm_buffer_sizes / lbm_batch_create /
+ * lbm_batch_buffer_sizes / lbm_mass_noalloc failure in this thread (those
+ * calls have no handle to store it in). */
 LBM_API const char *lbm_create_error(void);
 
 /* Free the handle's host state.  Bound buffers stay the caller's. */
 LBM_API void lbm_destroy(lbm_sim *sim);
+
+/* ------------------------------------------------------------------ batches
+ * The batched form: n independent domains, each with its own size and
+ * parameters (one dtype for the whole batch; every nx a multiple of 8),
+ * advanced together by ONE kernel launch per time step.  The launch walks a
+ * work list of (domain, 128-column strip, row segment) items with a
+ * persistent grid sized to the GPU's resident CTAs; items are sorted by
+ * decreasing cost.  Per-domain results are bit-identical to stepping each
+ * domain alone with lbm_step.  Fields and phi are concatenated in domain
+ * order, each domain row-major [ny][nx] in the field type.
+ */
+typedef struct lbm_batch lbm_batch; /* opaque handle, owned by the caller */
+
+/* Device bytes for the populations (two levels per domain) and the work
+ * buffer (domain and item tables, field staging, reduction partials). */
+LBM_API lbm_status lbm_batch_buffer_sizes(const lbm_params *prms, int n, size_t *state_bytes,
+                                          size_t *work_bytes);
+/* Validate every domain (as lbm_create) and create the handle; `stream`
+ * must be a non-default stream if graph replay is wanted. */
+LBM_API lbm_status lbm_batch_create(const lbm_params *prms, int n, void *stream,
+                                    lbm_batch **out);
+/* Bind caller-owned device buffers and upload the domain and item tables
+ * (synchronises the stream). */
+LBM_API lbm_status lbm_batch_bind_buffers(lbm_batch *b, void *state, size_t state_bytes,
+                                          void *work, size_t work_bytes);
+/* Equilibrium initial state of every domain from the concatenated phi
+ * (u = 0), device or host memory (on_host). */
+LBM_API lbm_status lbm_batch_init_phi(lbm_batch *b, const void *phi, int on_host);
+/* Advance every domain n steps: one launch per step, or, with graph replay
+ * on, two steps per replay of a captured CUDA graph. */
+LBM_API lbm_status lbm_batch_step(lbm_batch *b, int64_t n);
+/* Switch CUDA-graph replay of lbm_batch_step on (1) or off (0). */
+LBM_API lbm_status lbm_batch_set_graph(lbm_batch *b, int use_graph);
+/* Rows per work item (>= 16; default 64): the tile shape of the batch. */
+LBM_API lbm_status lbm_batch_set_segment(lbm_batch *b, int seg_h);
+/* Time candidate segment heights (16 .. 256) over `steps` steps each on the
+ * current state and keep the fastest.  The state advances by the timed
+ * steps; re-initialise afterwards if that matters. */
+LBM_API lbm_status lbm_batch_autotune(lbm_batch *b, int steps, int *seg_h_out, double *ms_out);
+/* Concatenated phi, ux, uy, p of the current time level (any may be NULL),
+ * device or host pointers (on_host; the stream is then synchronised). */
+LBM_API lbm_status lbm_batch_fields(lbm_batch *b, void *phi, void *ux, void *uy, void *p,
+                                    int on_host);
+/* Per-domain sum(rho) and sum(phi) (n doubles each, host), FP64. */
+LBM_API lbm_status lbm_batch_mass(lbm_batch *b, double *mass, double *phi_total);
+/* Total cells, steps taken, current segment height. */
+LBM_API int64_t lbm_batch_cells(const lbm_batch *b);
+LBM_API int64_t lbm_batch_step_count(const lbm_batch *b);
+LBM_API int lbm_batch_segment(const lbm_batch *b);
+LBM_API const char *lbm_batch_last_error(const lbm_batch *b);
+LBM_API void lbm_batch_destroy(lbm_batch *b);
 
 /* The mass diagnostic of lbm_mass for callers that cannot allocate device
  * memory.  The paper has no counterpart: this is a library convenience.

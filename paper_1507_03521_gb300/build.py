@@ -27,6 +27,7 @@ UNITS = {
     "lbm_f32": [],
     "lbm_f16": [],
     "lbm_noalloc": [],
+    "lbm_batch": [],
 }
 
 

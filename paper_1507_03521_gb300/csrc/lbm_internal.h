@@ -16,6 +16,11 @@ struct Derived {
     double grav, rhoref, tau_f, tau_g, uwb, uwt;
 };
 
+// One work item of the batched strip form (see lbm_strip.cuh).
+struct BatchItem {
+    int dom, x0, ys, ye;
+};
+
 // Launchers of one storage type.  All are asynchronous on `s` and return
 // the launch status (cudaGetLastError).
 struct Ops {
@@ -32,6 +37,14 @@ struct Ops {
     cudaError_t (*laplace)(const Derived &, const void *P, const void *phi, double xc, double yc,
                            double rin, double rout, double *part, int nblocks, double *out5,
                            cudaStream_t s);
+    // batched strip form
+    int strip_width;
+    bool (*strip_ok)(const Derived &);
+    size_t batch_dom_bytes;
+    void (*batch_fill_dom)(void *host_dst, const Derived &, long long off0, long long off1);
+    cudaError_t (*batch_slots)(int *slots);  // resident CTAs of one batch launch
+    cudaError_t (*batch_step)(char *state, const void *doms, const BatchItem *items, int nitems,
+                              int parity, int grid, cudaStream_t s);
 };
 
 const Ops *ops_f64();

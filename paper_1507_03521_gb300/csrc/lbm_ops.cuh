@@ -166,8 +166,53 @@ struct OpsImpl {
 
     static size_t level_bytes(long long NS) { return ST::level_bytes(NS); }
 
+    // ---- batched strip form
+    static void batch_fill_dom(void *host_dst, const Derived &d, long long off0, long long off1) {
+        BatchDom<T> b;
+        b.kp = make_kp<T>(d);
+        b.off[0] = off0;
+        b.off[1] = off1;
+        *static_cast<BatchDom<T> *>(host_dst) = b;
+    }
+
+    static cudaError_t batch_slots(int *slots) {
+        static int cache[64] = {};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev >= 64) return cudaErrorInvalidDevice;
+        if (!cache[dev]) {
+            e = cudaFuncSetAttribute(k_strip_batch<T, ST, SW, DEPTH>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
+            if (e != cudaSuccess) return e;
+            int per_sm = 0, sms = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_strip_batch<T, ST, SW, DEPTH>,
+                                                              SW, SM::bytes);
+            if (e != cudaSuccess) return e;
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+            if (per_sm < 1) return cudaErrorInvalidConfiguration;
+            cache[dev] = per_sm * sms;
+        }
+        *slots = cache[dev];
+        return cudaSuccess;
+    }
+
+    static cudaError_t batch_step(char *state, const void *doms, const BatchItem *items, int nitems,
+                                  int parity, int grid, cudaStream_t s) {
+        int slots = 0;
+        cudaError_t e = batch_slots(&slots);  // also sets the shared-memory attribute
+        if (e != cudaSuccess) return e;
+        k_strip_batch<T, ST, SW, DEPTH><<<grid, SW, SM::bytes, s>>>(
+            state, static_cast<const BatchDom<T> *>(doms), items, nitems, parity);
+        return cudaGetLastError();
+    }
+
     static const Ops *ops(const char *name) {
-        static const Ops o = {name, sizeof(T), &level_bytes, &step, &fields, &init, &mass, &laplace};
+        static const Ops o = {name,           sizeof(T),      &level_bytes,      &step,
+                              &fields,        &init,          &mass,             &laplace,
+                              SW,             &strip_ok,      sizeof(BatchDom<T>), &batch_fill_dom,
+                              &batch_slots,   &batch_step};
         return &o;
     }
 };

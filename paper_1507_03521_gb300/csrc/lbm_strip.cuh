@@ -24,6 +24,7 @@
 //     extrapolated from the two rows inside (same rules as k_step).
 #pragma once
 
+#include "lbm_internal.h"
 #include "lbm_kernels.cuh"
 
 namespace lbm {
@@ -294,20 +295,20 @@ __device__ __forceinline__ void columns(int t, F &&fn) {
     if ((t >> 5) == (XW % NW) && (t & 31) < 2 * H) fn(SW - H + (t & 31));
 }
 
+// One work item of the strip form: columns x0 .. x0+SW-1 (clipped to nx),
+// rows ys .. ye-1 of one domain, read from level `src`, written to `dst`.
+// The leading barrier also separates consecutive items of one CTA.
 template <class T, class ST, int SW, int DEPTH>
-__global__ void __launch_bounds__(SW)
-k_strip(const char *__restrict__ src, char *__restrict__ dst, const KP<T> P, int seg_h) {
+__device__ __forceinline__ void strip_body(const char *__restrict__ src, char *__restrict__ dst,
+                                           const KP<T> &P, const int x0, const int ys,
+                                           const int ye, char *smem_raw) {
     using SM = StripSmem<T, ST, SW, DEPTH>;
     using SR = typename SM::SR;
     constexpr int HP = SM::HP;
-    extern __shared__ __align__(16) char smem_raw[];
     const SM s(smem_raw);
     const int t = threadIdx.x;
     const int nx = P.nx, ny = P.ny, wall = P.wall;
     const int NS = (int)P.NS;
-    const int x0 = blockIdx.x * SW;
-    const int ys = blockIdx.y * seg_h;
-    const int ye = min(ys + seg_h, ny);
     const int yfirst = ys - 6;
 
     typename SR::Desc desc;
@@ -523,6 +524,50 @@ k_strip(const char *__restrict__ src, char *__restrict__ dst, const KP<T> P, int
         }
     }
     cp_async_wait<0>();
+}
+
+// Single domain: CTA (bx, by) owns strip bx and segment by.
+template <class T, class ST, int SW, int DEPTH>
+__global__ void __launch_bounds__(SW)
+k_strip(const char *__restrict__ src, char *__restrict__ dst, const __grid_constant__ KP<T> P,
+        int seg_h) {
+    extern __shared__ __align__(16) char smem_raw[];
+    const int ys = blockIdx.y * seg_h;
+    strip_body<T, ST, SW, DEPTH>(src, dst, P, blockIdx.x * SW, ys, min(ys + seg_h, P.ny),
+                                 smem_raw);
+}
+
+// ---------------------------------------------------------------- batches
+
+// A batch advances many independent domains (each with its own size and
+// parameters) in one launch per step.  Work items are (domain, strip,
+// segment); a persistent grid walks the item list, which the host sorts by
+// decreasing cost.
+template <class T>
+struct BatchDom {
+    KP<T> kp;
+    long long off[2];  // byte offsets of the domain's two levels in the state buffer
+};
+
+template <class T, class ST, int SW, int DEPTH>
+__global__ void __launch_bounds__(SW)
+k_strip_batch(char *__restrict__ state, const BatchDom<T> *__restrict__ doms,
+              const BatchItem *__restrict__ items, int nitems, int parity) {
+    extern __shared__ __align__(16) char smem_raw[];
+    __shared__ KP<T> sP;
+    __shared__ long long sOff[2];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem w = items[it];
+        __syncthreads();  // the previous item is done with sP
+        if (threadIdx.x == 0) {
+            sP = doms[w.dom].kp;
+            sOff[0] = doms[w.dom].off[parity];
+            sOff[1] = doms[w.dom].off[1 - parity];
+        }
+        __syncthreads();
+        strip_body<T, ST, SW, DEPTH>(state + sOff[0], state + sOff[1], sP, w.x0, w.ys, w.ye,
+                                     smem_raw);
+    }
 }
 
 }  // namespace lbm

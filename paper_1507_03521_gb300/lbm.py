@@ -27,7 +27,12 @@ STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_NONFI
 EXPORTS = ["lbm_version", "lbm_buffer_sizes", "lbm_create", "lbm_bind_buffers", "lbm_init_phi",
            "lbm_step", "lbm_fields", "lbm_mass", "lbm_laplace", "lbm_state_bytes",
            "lbm_get_state", "lbm_set_state", "lbm_step_count", "lbm_last_error",
-           "lbm_create_error", "lbm_destroy", "lbm_mass_noalloc"]
+           "lbm_create_error", "lbm_destroy", "lbm_mass_noalloc",
+           "lbm_batch_buffer_sizes", "lbm_batch_create", "lbm_batch_bind_buffers",
+           "lbm_batch_init_phi", "lbm_batch_step", "lbm_batch_set_graph", "lbm_batch_set_segment",
+           "lbm_batch_autotune", "lbm_batch_fields", "lbm_batch_mass", "lbm_batch_cells",
+           "lbm_batch_step_count", "lbm_batch_segment", "lbm_batch_last_error",
+           "lbm_batch_destroy"]
 
 
 class LBMError(RuntimeError):
@@ -99,6 +104,38 @@ def load(path: str = LIB_PATH):
     lib.lbm_destroy.argtypes = [_vp]
     lib.lbm_mass_noalloc.restype = S
     lib.lbm_mass_noalloc.argtypes = [ctypes.POINTER(CParams), _vp, _vp, _dp, _dp]
+    P = ctypes.POINTER(CParams)
+    lib.lbm_batch_buffer_sizes.restype = S
+    lib.lbm_batch_buffer_sizes.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t),
+                                           ctypes.POINTER(ctypes.c_size_t)]
+    lib.lbm_batch_create.restype = S
+    lib.lbm_batch_create.argtypes = [P, ctypes.c_int, _vp, ctypes.POINTER(_vp)]
+    lib.lbm_batch_bind_buffers.restype = S
+    lib.lbm_batch_bind_buffers.argtypes = [_vp, _vp, ctypes.c_size_t, _vp, ctypes.c_size_t]
+    lib.lbm_batch_init_phi.restype = S
+    lib.lbm_batch_init_phi.argtypes = [_vp, _vp, ctypes.c_int]
+    lib.lbm_batch_step.restype = S
+    lib.lbm_batch_step.argtypes = [_vp, ctypes.c_int64]
+    lib.lbm_batch_set_graph.restype = S
+    lib.lbm_batch_set_graph.argtypes = [_vp, ctypes.c_int]
+    lib.lbm_batch_set_segment.restype = S
+    lib.lbm_batch_set_segment.argtypes = [_vp, ctypes.c_int]
+    lib.lbm_batch_autotune.restype = S
+    lib.lbm_batch_autotune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]
+    lib.lbm_batch_fields.restype = S
+    lib.lbm_batch_fields.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]
+    lib.lbm_batch_mass.restype = S
+    lib.lbm_batch_mass.argtypes = [_vp, _dp, _dp]
+    lib.lbm_batch_cells.restype = ctypes.c_int64
+    lib.lbm_batch_cells.argtypes = [_vp]
+    lib.lbm_batch_step_count.restype = ctypes.c_int64
+    lib.lbm_batch_step_count.argtypes = [_vp]
+    lib.lbm_batch_segment.restype = ctypes.c_int
+    lib.lbm_batch_segment.argtypes = [_vp]
+    lib.lbm_batch_last_error.restype = ctypes.c_char_p
+    lib.lbm_batch_last_error.argtypes = [_vp]
+    lib.lbm_batch_destroy.restype = None
+    lib.lbm_batch_destroy.argtypes = [_vp]
     _lib = lib
     return lib
 
@@ -244,6 +281,114 @@ class Sim:
 
     def set_state(self, buf, step: int):
         self._check(self._lib.lbm_set_state(self._h, buf.data_ptr(), 0, int(step)))
+
+
+class Batch:
+    """Many independent domains advanced by one launch per step.
+
+    ``params_list``: parameter dicts (every nx a multiple of 8); ``dtype``
+    shared by all.  Runs on its own torch stream so that CUDA-graph replay
+    is possible.  Fields come back as a list of per-domain tensors.
+    """
+
+    def __init__(self, params_list, dtype="f32", device=None, graph=False):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblbm needs a CUDA device; none is available")
+        self._lib = load()
+        self.dtype = dtype
+        self.params = [dict(p) for p in params_list]
+        self.n = len(self.params)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = torch.cuda.Stream(self.device)
+        self.field_dtype = torch.float64 if dtype == "f64" else torch.float32
+        arr = (CParams * self.n)(*[make_params(p, dtype) for p in self.params])
+        self._arr = arr
+        sb, wb = ctypes.c_size_t(), ctypes.c_size_t()
+        st = self._lib.lbm_batch_buffer_sizes(arr, self.n, ctypes.byref(sb), ctypes.byref(wb))
+        if st != 0:
+            raise LBMError(st, self._lib.lbm_create_error().decode())
+        h = _vp()
+        st = self._lib.lbm_batch_create(arr, self.n, _vp(self.stream.cuda_stream), ctypes.byref(h))
+        if st != 0:
+            raise LBMError(st, self._lib.lbm_create_error().decode())
+        self._h = h
+        self.state_buf = torch.empty(sb.value, dtype=torch.uint8, device=self.device)
+        self.work_buf = torch.empty(wb.value, dtype=torch.uint8, device=self.device)
+        torch.cuda.synchronize(self.device)
+        self._check(self._lib.lbm_batch_bind_buffers(h, self.state_buf.data_ptr(), sb.value,
+                                                     self.work_buf.data_ptr(), wb.value))
+        if graph:
+            self._check(self._lib.lbm_batch_set_graph(h, 1))
+        self.shapes = [(p["ny"], p["nx"]) for p in self.params]
+        self.offsets = np.concatenate([[0], np.cumsum([a * b for a, b in self.shapes])])
+
+    def _check(self, st):
+        if st != 0:
+            raise LBMError(st, self._lib.lbm_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.stream.synchronize()
+            self._lib.lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def cells(self) -> int:
+        return self._lib.lbm_batch_cells(self._h)
+
+    @property
+    def step_count(self) -> int:
+        return self._lib.lbm_batch_step_count(self._h)
+
+    @property
+    def segment(self) -> int:
+        return self._lib.lbm_batch_segment(self._h)
+
+    def init_phi(self, phis):
+        import torch
+        flat = np.concatenate([np.ascontiguousarray(p, dtype=np.float64).ravel() for p in phis])
+        t = torch.from_numpy(flat).to(device=self.device, dtype=self.field_dtype)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        self._keep = t
+        self._check(self._lib.lbm_batch_init_phi(self._h, t.data_ptr(), 0))
+
+    def step(self, n=1):
+        self._check(self._lib.lbm_batch_step(self._h, int(n)))
+
+    def set_segment(self, seg_h):
+        self._check(self._lib.lbm_batch_set_segment(self._h, int(seg_h)))
+
+    def autotune(self, steps=3):
+        seg, ms = ctypes.c_int(), ctypes.c_double()
+        self._check(self._lib.lbm_batch_autotune(self._h, int(steps), ctypes.byref(seg),
+                                                 ctypes.byref(ms)))
+        return seg.value, ms.value
+
+    def fields(self):
+        import torch
+        out = {k: torch.empty(int(self.offsets[-1]), dtype=self.field_dtype, device=self.device)
+               for k in ("phi", "ux", "uy", "p")}
+        self._check(self._lib.lbm_batch_fields(self._h, out["phi"].data_ptr(), out["ux"].data_ptr(),
+                                               out["uy"].data_ptr(), out["p"].data_ptr(), 0))
+        self.stream.synchronize()
+        res = []
+        for i, (ny, nx) in enumerate(self.shapes):
+            a, b = int(self.offsets[i]), int(self.offsets[i + 1])
+            res.append({k: v[a:b].reshape(ny, nx) for k, v in out.items()})
+        return res
+
+    def mass(self):
+        m = np.zeros(self.n)
+        t = np.zeros(self.n)
+        self._check(self._lib.lbm_batch_mass(self._h, m.ctypes.data_as(_dp), t.ctypes.data_as(_dp)))
+        return m, t
 
 
 @dataclass

@@ -180,3 +180,29 @@ def small_case(nx, ny, seed, walls=False, gravity=0.0, u_wall=0.0, rho_ratio=10.
     ux = 0.01 * rng.standard_normal((ny, nx))
     uy = 0.01 * rng.standard_normal((ny, nx))
     return p, phi, ux, uy
+
+
+def batch_domains(n=1024, seed=1507036, sides=tuple(range(64, 513, 32)), max_side=None):
+    """n independent periodic domains: nx, ny uniform over `sides`; half
+    hold a centred tanh droplet of radius U[0.2, 0.35] x min side, half a
+    flat layer of fluid A in ny/4 <= y < 3ny/4 (Sec. 4.1 shape); rho_A = 1,
+    rho_A/rho_B log-uniform in [1, 100]; sigma U[1e-4, 1e-2]; M U[0.01, 0.2];
+    tau = 0.8; phi in [-1, 1]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sides = [s for s in sides if max_side is None or s <= max_side]
+    out = []
+    for _ in range(n):
+        nx = int(rng.choice(sides))
+        ny = int(rng.choice(sides))
+        ratio = float(np.exp(rng.uniform(0.0, np.log(100.0))))
+        sigma = float(rng.uniform(1e-4, 1e-2))
+        M = float(rng.uniform(0.01, 0.2))
+        p = _base(nx=nx, ny=ny, rho_A=1.0, rho_B=1.0 / ratio, sigma=sigma, W=4.0, M=M,
+                  tau_f=0.8, tau_g=0.8)
+        if rng.uniform() < 0.5:
+            R = float(rng.uniform(0.2, 0.35)) * min(nx, ny)
+            phi = droplet_field(nx, ny, nx / 2.0, ny / 2.0, R, 4.0, 1.0, -1.0)
+        else:
+            phi = layer_field(nx, ny, ny / 4.0, 3.0 * ny / 4.0 - 1.0, 4.0, 1.0, -1.0)
+        out.append((p, phi))
+    return out

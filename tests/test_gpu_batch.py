@@ -1,0 +1,125 @@
+"""The batched form (one launch per step over many domains) against the
+single-domain path and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1507_03521_gb300 import workloads as W
+from helpers import check64, oracle_spread
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1507_03521_gb300 import build, lbm
+    build.build()
+    return lbm
+
+
+def _mixed():
+    """Domains of different sizes (nx % 8 == 0), parameters and boundaries."""
+    doms = W.batch_domains(n=9, seed=77, sides=(64, 96, 136, 200, 256))
+    p, phi, _, _ = W.small_case(48, 37, seed=3, walls=True, gravity=1e-5, u_wall=0.01)
+    doms.append((p, phi))
+    p, phi, _, _ = W.small_case(16, 9, seed=4, walls=True, gravity=-1e-5, u_wall=-0.02)
+    doms.append((p, phi))
+    p, phi, _, _ = W.small_case(8, 70, seed=5)
+    doms.append((p, phi))
+    return doms
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16s", "f64"])
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_equals_single_domain_runs(L, dtype, graph):
+    """Same kernel body per item: every domain of the batch is bit-identical
+    to stepping it alone, with or without CUDA-graph replay, for an odd
+    step count (so both parities and a plain launch occur)."""
+    doms = _mixed()
+    b = L.Batch([p for p, _ in doms], dtype, graph=graph)
+    b.init_phi([phi for _, phi in doms])
+    b.step(7)
+    got = b.fields()
+    m, t = b.mass()
+    for i, (p, phi) in enumerate(doms):
+        s = L.Sim(p, dtype)
+        s.init_phi(phi)
+        s.step(7)
+        ref = s.fields(("phi", "ux", "uy", "p"))
+        for k in ("phi", "ux", "uy", "p"):
+            assert np.array_equal(got[i][k].cpu().numpy(), ref[k].cpu().numpy()), (i, k)
+        sm, st = s.mass()
+        assert m[i] == sm and t[i] == st
+    assert b.step_count == 7
+    b.close()
+
+
+def test_batch_segment_choice_does_not_change_results(L):
+    doms = _mixed()
+    res = []
+    for seg in (16, 40, 256):
+        b = L.Batch([p for p, _ in doms], "f32")
+        b.set_segment(seg)
+        b.init_phi([phi for _, phi in doms])
+        b.step(5)
+        res.append([f["phi"].cpu().numpy() for f in b.fields()])
+        b.close()
+    for a, c in zip(res[0], res[1]):
+        assert np.array_equal(a, c)
+    for a, c in zip(res[0], res[2]):
+        assert np.array_equal(a, c)
+
+
+def test_batch_matches_oracle(L):
+    """16 seeded domains of the batch workload's distribution (sides up to
+    256 here), FP64, 60 steps, element by element against the oracle.  The
+    distribution includes parameter sets on which the scheme itself diverges
+    (e.g. rho ratio 84 with sigma = 7.5e-3): there the oracle's fields turn
+    non-finite, and the GPU's must as well."""
+    doms = W.batch_domains(n=16, seed=1507036, max_side=256)
+    b = L.Batch([p for p, _ in doms], "f64")
+    b.init_phi([phi for _, phi in doms])
+    b.step(60)
+    got = b.fields()
+    finite = 0
+    for i, (p, phi) in enumerate(doms):
+        o = oracle.Oracle(p)
+        o.init_phi(phi)
+        o.step(60)
+        ref = o.fields()
+        if not all(np.isfinite(ref[k]).all() for k in ("phi", "ux", "uy", "p")):
+            assert not np.isfinite(got[i]["phi"].cpu().numpy()).all(), i
+            continue
+        finite += 1
+        g = {k: got[i][k].cpu().numpy() for k in ("phi", "ux", "uy", "p")}
+        check64(g, ref, oracle_spread(p, phi, None, None, 60, ref), f"domain {i}",
+                keys=("phi", "ux", "uy", "p"))
+    assert finite >= 12
+
+
+def test_batch_autotune_keeps_results(L):
+    doms = _mixed()
+    b = L.Batch([p for p, _ in doms], "f32", graph=True)
+    b.init_phi([phi for _, phi in doms])
+    seg, ms = b.autotune(steps=2)
+    assert seg in (16, 24, 32, 48, 64, 96, 128, 192, 256) and ms > 0
+    assert b.segment == seg
+    b.init_phi([phi for _, phi in doms])
+    b.step(4)
+    got = [f["phi"].cpu().numpy() for f in b.fields()]
+    ref = L.Batch([p for p, _ in doms], "f32")
+    ref.init_phi([phi for _, phi in doms])
+    ref.step(4)
+    for a, c in zip(got, [f["phi"].cpu().numpy() for f in ref.fields()]):
+        assert np.array_equal(a, c)
+
+
+def test_batch_rejects_bad_domains(L):
+    p, phi = W.droplet64()
+    with pytest.raises(L.LBMError):
+        L.Batch([p, dict(p, nx=37)], "f32")
+    with pytest.raises(L.LBMError):
+        L.Batch([p, dict(p, tau_f=0.5)], "f32")
