@@ -228,6 +228,42 @@ def measure_batch(lbm, W, args, peak, dist):
             "launches_per_step": 1, "kernel": "k_strip_batch<float>"}
 
 
+def measure_adjoint(W):
+    """Adjoint workload: droplet in shear, 512 x 512, R = 64, walls at
+    +-0.01, rho ratio 10, FP32, 4000 steps, checkpoints every 200 steps;
+    loss = sum (phi_T - phi_target)^2 with phi_target from a run at
+    (1.05 M, 0.95 sigma).  Times the forward (with checkpoints) and the
+    backward (recompute + hand-written adjoint + initial-state adjoint)."""
+    import torch
+    from paper_1507_03521_gb300 import lbm
+    from paper_1507_03521_gb300.adjoint import rollout_loss
+    steps, K = 4000, 200
+    p, phi = W.shear_droplet(512, 64.0)
+    s = lbm.Sim(dict(p, M=1.05 * p["M"], sigma=0.95 * p["sigma"]), "f32")
+    s.init_phi(phi)
+    s.step(steps)
+    target = s.fields(("phi",))["phi"].double().cpu()
+    s.close()
+    ph = torch.from_numpy(phi).clone().requires_grad_(True)
+    M = torch.tensor(p["M"], dtype=torch.float64, requires_grad=True)
+    sg = torch.tensor(p["sigma"], dtype=torch.float64, requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = rollout_loss(ph, M, sg, p, steps, target, K=K, dtype="f32")
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    cells = 512 * 512
+    return {"workload": "shear-droplet-512x512-4000steps", "dtype": "f32", "checkpoint_every": K,
+            "loss": loss.item(), "dL_dM": M.grad.item(), "dL_dsigma": sg.grad.item(),
+            "dL_dphi0_norm": float(ph.grad.norm()),
+            "forward_s": round(t1 - t0, 4), "backward_s": round(t2 - t1, 4),
+            "backward_mlups": round(cells * steps / (t2 - t1) / 1e6, 2),
+            "note": "wall-clock incl. host loop; backward = recompute + adjoint steps"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -238,6 +274,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the f16s/bf16s/f64 forms")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -347,6 +384,8 @@ def main():
 
     if not args.no_batch:
         line["batched"] = measure_batch(lbm, W, args, peak, dist)
+    if not args.no_adjoint:
+        line["adjoint"] = measure_adjoint(W)
 
     # End to end through the C ABI with host buffers: phi0 in, K steps,
     # phi/u/p out and the mass diagnostic, all inside the timed region.

@@ -171,6 +171,34 @@ LBM_API const char *lbm_create_error(void);
 /* Free the handle's host state.  Bound buffers stay the caller's. */
 LBM_API void lbm_destroy(lbm_sim *sim);
 
+/* ------------------------------------------------------------------ adjoint
+ * Hand-written discrete adjoint (vector-Jacobian product) of the step, for
+ * LBM_F64 and LBM_F32 handles.  With s_t the populations after t steps
+ * (one level, the layout lbm_get_state writes) and lambda_t = dL/ds_t for
+ * the loss L = sum_x (phi_T(x) - phi_target(x))^2:
+ *   lbm_adj_seed   lambda_T from s_T and phi_target (and L itself);
+ *   lbm_adj_step   lambda_t from s_t and lambda_{t+1}, adding the step's
+ *                  contributions to dL/dM and dL/dsigma;
+ *   lbm_adj_init   dL/dphi0 from lambda_0 (adjoint of lbm_init_phi with
+ *                  u = 0), adding its (M, sigma) contributions;
+ *   lbm_adj_grads  read the accumulated dL/dM, dL/dsigma.
+ * M is the mobility lambda (alpha = M / (cs2 (tau_g - 1/2))), sigma the
+ * surface tension (kappa and beta proportional to it).  All pointers are
+ * device pointers; state and lambda buffers are lbm_state_bytes() each and
+ * lam_next must differ from lam_t.  `work` is a caller-owned device buffer
+ * of lbm_adj_work_bytes() bytes, 256-byte aligned, holding scratch fields
+ * and the running totals (lbm_adj_reset zeroes them).  Asynchronous on the
+ * handle's stream except lbm_adj_grads and a seed that returns the loss. */
+LBM_API lbm_status lbm_adj_work_bytes(const lbm_sim *sim, size_t *bytes);
+LBM_API lbm_status lbm_adj_reset(lbm_sim *sim, void *work);
+LBM_API lbm_status lbm_adj_seed(lbm_sim *sim, const void *state_T, const void *phi_target,
+                                void *lam_T, void *work, double *loss);
+LBM_API lbm_status lbm_adj_step(lbm_sim *sim, const void *state_t, const void *lam_next,
+                                void *lam_t, void *work);
+LBM_API lbm_status lbm_adj_init(lbm_sim *sim, const void *phi0, const void *lam_0,
+                                void *phi0_bar, void *work);
+LBM_API lbm_status lbm_adj_grads(lbm_sim *sim, void *work, double *dM, double *dsigma);
+
 /* ------------------------------------------------------------------ batches
  * The batched form: n independent domains, each with its own size and
  * parameters (one dtype for the whole batch; every nx a multiple of 8),

@@ -1,0 +1,72 @@
+"""Gradients of an interface-shape loss through many time steps.
+
+``rollout_loss(phi0, M, sigma, params, steps, target)`` returns
+L = sum_x (phi_T(x) - target(x))^2 after `steps` steps from the
+equilibrium state of phi0 (u = 0), as a torch scalar that supports
+backward() with respect to phi0, M (mobility lambda) and sigma (surface
+tension).  Forward and backward run in the CUDA library: the forward keeps
+a checkpoint every K steps; the backward recomputes each segment of K steps
+from its checkpoint, then applies the hand-written adjoint step
+(lbm_adj_step) K times in reverse, and finally the adjoint of the initial
+state (lbm_adj_init).  Memory: steps/K checkpoints plus K states.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import lbm
+
+
+class LBMRollout(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, phi0, M, sigma, params, steps, target, K, dtype):
+        p = dict(params, M=float(M), sigma=float(sigma))
+        sim = lbm.Sim(p, dtype)
+        sim.init_phi(phi0.detach())
+        ckpt = []
+        for t in range(steps):
+            if t % K == 0:
+                ckpt.append(sim.get_state()[0])
+            sim.step(1)
+        state_T, _ = sim.get_state()
+        work = sim.adj_work()
+        lam = torch.empty_like(state_T)
+        loss = sim.adj_seed(state_T, target.detach(), lam, work)
+        ctx.sim, ctx.ckpt, ctx.lam, ctx.work = sim, ckpt, lam, work
+        ctx.steps, ctx.K = steps, K
+        ctx.save_for_backward(phi0.detach())
+        return torch.tensor(loss, dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        sim, lam, work = ctx.sim, ctx.lam, ctx.work
+        (phi0,) = ctx.saved_tensors
+        other = torch.empty_like(lam)
+        steps, K = ctx.steps, ctx.K
+        for seg in reversed(range(len(ctx.ckpt))):
+            t0 = seg * K
+            n = min(K, steps - t0)
+            sim.set_state(ctx.ckpt[seg], t0)
+            states = []
+            for _ in range(n):
+                states.append(sim.get_state()[0])
+                sim.step(1)
+            for k in reversed(range(n)):
+                sim.adj_step(states[k], lam, other, work)
+                lam, other = other, lam
+        phi_bar = sim.adj_init(phi0, lam, work)
+        dM, dS = sim.adj_grads(work)
+        g = float(grad_out)
+        sim.close()
+        return (phi_bar.to(device=phi0.device, dtype=phi0.dtype) * g,
+                torch.tensor(dM * g, dtype=torch.float64),
+                torch.tensor(dS * g, dtype=torch.float64), None, None, None, None, None)
+
+
+def rollout_loss(phi0, M, sigma, params, steps, target, K=200, dtype="f64"):
+    """L = sum (phi_T - target)^2; differentiable in phi0, M, sigma."""
+    if not torch.is_tensor(M):
+        M = torch.tensor(float(M), dtype=torch.float64)
+    if not torch.is_tensor(sigma):
+        sigma = torch.tensor(float(sigma), dtype=torch.float64)
+    return LBMRollout.apply(phi0, M, sigma, params, int(steps), target, int(K), dtype)

@@ -1,0 +1,562 @@
+// lbm_adjoint.cuh — hand-written discrete adjoint (vector-Jacobian product)
+// of one time step, of the equilibrium initial state and of the loss
+// L = sum (phi_T - phi_target)^2, for FP64 / FP32 populations in the plain
+// layout.
+//
+// With s_t the populations at step t and lambda_t = dL/ds_t:
+//   lambda_t = (d s_{t+1} / d s_t)^T lambda_{t+1},
+//   dL/dM, dL/dsigma += (d s_{t+1} / d(M, sigma))^T lambda_{t+1}.
+// The forward step (Sec. 3) is a chain of local maps and stencils:
+//   phi = sum g, rho(phi)            (Eqs. 30, 11)
+//   mu = psi'(phi) - kappa lap phi   (Eq. 5)
+//   grad phi, grad mu, lap mu; F; u; p (Eqs. 31-32)
+//   grad p; collision (Eqs. 22-29); streaming / bounce-back.
+// The adjoint runs the chain backwards.  Local maps are differentiated by
+// hand; every stencil is applied transposed as a gather (each cell collects
+// from the cells whose stencils read it, with the ghost-row rules of the
+// forward step: mirror for phi and mu, linear extrapolation for p), so the
+// result is deterministic.  Kernels, in order, for one reverse step:
+//   k_adj_f0 .. k_adj_f3  recompute the forward fields of step t,
+//   k_adj_collide         streaming and collision transposed,
+//   k_adj_p               grad p transposed, then u, p, F backwards,
+//   k_adj_mu              grad mu and lap mu transposed,
+//   k_adj_phi             grad phi and lap phi transposed, phi = sum g,
+//   k_adj_theta           per-cell (M, sigma) terms reduced in FP64.
+// M enters through alpha = M / (cs2 (tau_g - 1/2)) and gamma lambda with
+// lambda = M (Eq. 33); sigma through kappa and beta, both proportional to
+// sigma (Eqs. 3-4 solved), so mu = sigma mu1.
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+template <class T>
+struct AdjP {
+    KP<T> k;
+    T alpha1;  // alpha per unit M
+    T gamma;   // gamma (Eq. 17)
+    T kappa1, beta1;  // kappa, beta per unit sigma
+};
+
+// Work arrays of the adjoint, each N (padded NS) elements of T.
+enum AdjArr {
+    A_PHI, A_RHO, A_MU, A_MU1, A_GPHX, A_GPHY, A_GMUX, A_GMUY, A_LMU, A_FX, A_FY, A_UX, A_UY,
+    A_P, A_GPX, A_GPY,
+    B_P, B_RHO, B_PHI, B_MU, B_UX, B_UY, B_FX, B_FY, B_GRX, B_GRY, B_LMU, B_GPX, B_GPY,
+    B_GPHX, B_GPHY, B_GMUX, B_GMUY, B_ALPHA, B_GL, B_SIGMA,
+    A_COUNT
+};
+
+template <class T>
+struct AdjW {
+    T *a;          // A_COUNT arrays of NS elements
+    long long NS;
+    __device__ __forceinline__ T *operator[](int k) const { return a + (long long)k * NS; }
+};
+
+// ------------------------------------------------------------- helpers
+
+template <class T>
+struct Nb {
+    int nx, ny, wall;
+    // periodic x
+    __device__ __forceinline__ int wx(int x) const { return x < 0 ? x + nx : (x >= nx ? x - nx : x); }
+    // row of a stencil read at row y: periodic wrap or mirror
+    __device__ __forceinline__ int my(int y) const {
+        if (!wall) return y < 0 ? y + ny : (y >= ny ? y - ny : y);
+        return y < 0 ? -y - 1 : (y >= ny ? 2 * ny - 1 - y : y);
+    }
+};
+
+// Forward isotropic gradient / Laplacian at (x, y) of a global array with
+// mirror ghosts (extrap = false) or linear-extrapolation ghosts (p).
+template <class T>
+__device__ __forceinline__ T nbval(const T *v, const Nb<T> &B, int x, int y, bool extrap) {
+    const int xx = B.wx(x);
+    if (!B.wall || (y >= 0 && y < B.ny)) return v[(long long)B.my(y) * B.nx + xx];
+    if (!extrap) return v[(long long)B.my(y) * B.nx + xx];
+    if (y < 0) return T(2) * v[xx] - v[(long long)B.nx + xx];
+    return T(2) * v[(long long)(B.ny - 1) * B.nx + xx] - v[(long long)(B.ny - 2) * B.nx + xx];
+}
+
+template <class T>
+__device__ __forceinline__ void grad_g(const T *v, const Nb<T> &B, int x, int y, bool extrap, T &gx,
+                                       T &gy) {
+    T sx = T(0), sy = T(0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const T n = nbval(v, B, x + D2Q9::cx(i), y + D2Q9::cy(i), extrap);
+        sx += T(3.0 * D2Q9::w(i) * D2Q9::cx(i)) * n;
+        sy += T(3.0 * D2Q9::w(i) * D2Q9::cy(i)) * n;
+    }
+    gx = sx;
+    gy = sy;
+}
+
+template <class T>
+__device__ __forceinline__ T lap_g(const T *v, const Nb<T> &B, int x, int y) {
+    const T c = v[(long long)y * B.nx + x];
+    T acc = T(0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+        acc += T(6.0 * D2Q9::w(i)) * (nbval(v, B, x + D2Q9::cx(i), y + D2Q9::cy(i), false) - c);
+    return acc;
+}
+
+// Transposed stencil as a gather at target (x, y): the sum over every
+// (centre c, direction i) whose forward read of direction i lands on the
+// target, of coef * term(c, i); coef follows the ghost rule (1 for a direct
+// or mirrored read; 2 and -1 for the two rows an extrapolated ghost uses).
+template <class T, class F>
+__device__ __forceinline__ T tgather(const Nb<T> &B, int x, int y, bool extrap, F &&term) {
+    T acc = T(0);
+    const int nx = B.nx, ny = B.ny;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const int cx = D2Q9::cx(i), cy = D2Q9::cy(i);
+        const int sx = B.wx(x - cx);
+        int sy = y - cy;
+        if (!B.wall) {
+            sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+            acc += term((long long)sy * nx + sx, i, T(1));
+            continue;
+        }
+        if (sy >= 0 && sy < ny) acc += term((long long)sy * nx + sx, i, T(1));
+        // ghost reads: centre on the edge row, direction pointing out of it
+        if (cy == -1) {
+            if (!extrap) {
+                if (y == 0) acc += term((long long)sx, i, T(1));
+            } else {
+                if (y == 0) acc += term((long long)sx, i, T(2));
+                if (y == 1) acc += term((long long)sx, i, T(-1));
+            }
+        } else if (cy == 1) {
+            const long long top = (long long)(ny - 1) * nx + sx;
+            if (!extrap) {
+                if (y == ny - 1) acc += term(top, i, T(1));
+            } else {
+                if (y == ny - 1) acc += term(top, i, T(2));
+                if (y == ny - 2) acc += term(top, i, T(-1));
+            }
+        }
+    }
+    return acc;
+}
+
+#define ADJ_LOOP(k, N)                                                            \
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < (N); \
+         k += (long long)gridDim.x * blockDim.x)
+
+// ----------------------------------------------------- forward recompute
+
+// phi, rho, and (temporarily) sum f, j in A_P, A_UX, A_UY.
+template <class T>
+__global__ void k_adj_f0(const T *__restrict__ lvl, const AdjP<T> P, AdjW<T> W) {
+    const long long N = (long long)P.k.nx * P.k.ny, NS = P.k.NS;
+    ADJ_LOOP(k, N) {
+        T f[9], g[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            f[i] = lvl[i * NS + k];
+            g[i] = lvl[(9 + i) * NS + k];
+        }
+        T phi = T(0), ps = T(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            phi += g[i];
+            ps += f[i];
+        }
+        W[A_PHI][k] = phi;
+        W[A_RHO][k] = P.k.rhoB + (phi - P.k.phiB) * P.k.drho;
+        W[A_P][k] = ps;
+        W[A_UX][k] = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+        W[A_UY][k] = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
+    }
+}
+
+// phi given directly (initial state): copy into A_PHI.
+template <class T>
+__global__ void k_adj_phi0(const T *__restrict__ phi0, const AdjP<T> P, AdjW<T> W) {
+    const long long N = (long long)P.k.nx * P.k.ny;
+    ADJ_LOOP(k, N) W[A_PHI][k] = phi0[k];
+}
+
+// mu, mu per unit sigma, grad phi.
+template <class T>
+__global__ void k_adj_f1(const AdjP<T> P, AdjW<T> W) {
+    const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
+    const long long N = (long long)P.k.nx * P.k.ny;
+    ADJ_LOOP(k, N) {
+        const int y = (int)(k / B.nx), x = (int)(k - (long long)y * B.nx);
+        const T ph = W[A_PHI][k];
+        const T lap = lap_g(W[A_PHI], B, x, y);
+        const T q = (ph - P.k.phiA) * (ph - P.k.phiB) * (ph - P.k.phibar);
+        W[A_MU][k] = P.k.beta4 * q - P.k.kappa * lap;
+        W[A_MU1][k] = T(4) * P.beta1 * q - P.kappa1 * lap;
+        T gx, gy;
+        grad_g(W[A_PHI], B, x, y, false, gx, gy);
+        W[A_GPHX][k] = gx;
+        W[A_GPHY][k] = gy;
+    }
+}
+
+// grad mu, lap mu, F, u, p (Eqs. 31-32); A_UX/A_UY/A_P hold j and sum f.
+template <class T>
+__global__ void k_adj_f2(const AdjP<T> P, AdjW<T> W) {
+    const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
+    const long long N = (long long)P.k.nx * P.k.ny;
+    ADJ_LOOP(k, N) {
+        const int y = (int)(k / B.nx), x = (int)(k - (long long)y * B.nx);
+        T gx, gy;
+        grad_g(W[A_MU], B, x, y, false, gx, gy);
+        const T lm = lap_g(W[A_MU], B, x, y);
+        const T ph = W[A_PHI][k], rho = W[A_RHO][k];
+        const T Fx = -ph * gx;
+        const T Fy = -ph * gy - (rho - P.k.rhoref) * P.k.grav;
+        const T ux = (W[A_UX][k] + Fx / T(6)) * T(3) / rho;
+        const T uy = (W[A_UY][k] + Fy / T(6)) * T(3) / rho;
+        const T udr = P.k.drho * (ux * W[A_GPHX][k] + uy * W[A_GPHY][k]);
+        W[A_P][k] = W[A_P][k] + (udr - P.k.gl * rho * lm) / T(6);
+        W[A_GMUX][k] = gx;
+        W[A_GMUY][k] = gy;
+        W[A_LMU][k] = lm;
+        W[A_FX][k] = Fx;
+        W[A_FY][k] = Fy;
+        W[A_UX][k] = ux;
+        W[A_UY][k] = uy;
+    }
+}
+
+// grad p with extrapolated ghosts.
+template <class T>
+__global__ void k_adj_f3(const AdjP<T> P, AdjW<T> W) {
+    const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
+    const long long N = (long long)P.k.nx * P.k.ny;
+    ADJ_LOOP(k, N) {
+        const int y = (int)(k / B.nx), x = (int)(k - (long long)y * B.nx);
+        T gx, gy;
+        grad_g(W[A_P], B, x, y, true, gx, gy);
+        W[A_GPX][k] = gx;
+        W[A_GPY][k] = gy;
+    }
+}
+
+// ------------------------------------------------------------ reverse
+
+// Streaming and collision transposed.  lam_next: lambda_{t+1}; lam: output
+// lambda_t (partial: the direct (1 - 1/tau) terms; k_adj_p and k_adj_phi
+// add the terms through p, j and phi).
+template <class T>
+__global__ void k_adj_collide(const T *__restrict__ lam_next, T *__restrict__ lam, const AdjP<T> P,
+                              AdjW<T> W) {
+    const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
+    const long long N = (long long)P.k.nx * P.k.ny, NS = P.k.NS;
+    const KP<T> &K = P.k;
+    ADJ_LOOP(k, N) {
+        const int y = (int)(k / B.nx), x = (int)(k - (long long)y * B.nx);
+        const T phi = W[A_PHI][k], rho = W[A_RHO][k], mu = W[A_MU][k], p = W[A_P][k];
+        const T ux = W[A_UX][k], uy = W[A_UY][k], Fx = W[A_FX][k], Fy = W[A_FY][k];
+        const T grx = K.drho * W[A_GPHX][k], gry = K.drho * W[A_GPHY][k];
+        const T lm = W[A_LMU][k], gpx = W[A_GPX][k], gpy = W[A_GPY][k];
+        const T uu = ux * ux + uy * uy;
+        const T q = -T(3) * phi / rho;
+        const T Dx = gpx - Fx, Dy = gpy - Fy;
+        T bp = 0, brho = 0, bphi = 0, bmu = 0, bux = 0, buy = 0, bFx = 0, bFy = 0, bgrx = 0,
+          bgry = 0, blm = 0, bgpx = 0, bgpy = 0, balpha = 0, bgl = 0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int cx = D2Q9::cx(i), cy = D2Q9::cy(i);
+            const T w = T(D2Q9::w(i));
+            // lambda of the post-collision population: where streaming put it
+            const int yd = y + cy;
+            T lf, lg;
+            if (B.wall && (yd < 0 || yd >= B.ny)) {
+                const int o = D2Q9::opp(i);
+                lf = lam_next[o * NS + k];
+                lg = lam_next[(9 + o) * NS + k];
+                const T cuw = T(cx) * (yd < 0 ? K.uwb : K.uwt);
+                brho += -T(2) * w * cuw * lf;   // f_opp = f*_i - 2 w rho c.u_w
+                bphi += -T(6) * w * cuw * lg;   // g_opp = g*_i - 2 w phi c.u_w / cs2
+            } else {
+                const int xx = B.wx(x + cx);
+                const int yy = yd < 0 ? yd + B.ny : (yd >= B.ny ? yd - B.ny : yd);
+                const long long kd = (long long)yy * B.nx + xx;
+                lf = lam_next[i * NS + kd];
+                lg = lam_next[(9 + i) * NS + kd];
+            }
+            lam[i * NS + k] = (T(1) - K.itf) * lf;
+            lam[(9 + i) * NS + k] = (T(1) - K.itg) * lg;
+            const T beq = K.itf * lf, bF = K.pf * lf;    // d/d f^eq_i, d/d F_i
+            const T bgeq = K.itg * lg, bG = K.pg * lg;   // d/d g^eq_i, d/d G_i
+            const T cu = T(cx) * ux + T(cy) * uy;
+            const T s = T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu;
+            const T ex = T(cx) - ux, ey = T(cy) - uy;
+            T bs = 0;
+            // f^eq_i = w (p + rho s / 3)   (Eq. 24)
+            bp += w * beq;
+            brho += w * s / T(3) * beq;
+            bs += w * rho / T(3) * beq;
+            // g^eq_i = H_i + w phi s   (Eqs. 25, 27)
+            if (i == 0) {
+                bphi += bgeq;
+                bmu += -T(1.0 - D2Q9::w(0)) * K.alpha * bgeq;
+                balpha += -T(1.0 - D2Q9::w(0)) * mu * bgeq;
+            } else {
+                bmu += w * K.alpha * bgeq;
+                balpha += w * mu * bgeq;
+            }
+            bphi += w * s * bgeq;
+            bs += w * phi * bgeq;
+            // F_i = (c - u).[w (1 + s) F + w s grad rho / 3] - w rho gamma lambda lap mu / 3
+            const T eF = ex * Fx + ey * Fy, eR = ex * grx + ey * gry;
+            const T Ax = w * (T(1) + s) * Fx + w * s * grx / T(3);
+            const T Ay = w * (T(1) + s) * Fy + w * s * gry / T(3);
+            bFx += w * (T(1) + s) * ex * bF;
+            bFy += w * (T(1) + s) * ey * bF;
+            bgrx += w * s / T(3) * ex * bF;
+            bgry += w * s / T(3) * ey * bF;
+            bs += w * (eF + eR / T(3)) * bF;
+            bux += -Ax * bF;
+            buy += -Ay * bF;
+            brho += -w / T(3) * K.gl * lm * bF;
+            blm += -w / T(3) * rho * K.gl * bF;
+            bgl += -w / T(3) * rho * lm * bF;
+            // G_i = q w (1 + s) (c - u).(grad p - F), q = -phi / (cs2 rho)
+            const T E = ex * Dx + ey * Dy;
+            const T wg = w * (T(1) + s);
+            bphi += -T(3) / rho * wg * E * bG;
+            brho += T(3) * phi / (rho * rho) * wg * E * bG;
+            bs += q * w * E * bG;
+            bux += -q * wg * Dx * bG;
+            buy += -q * wg * Dy * bG;
+            bgpx += q * wg * ex * bG;
+            bgpy += q * wg * ey * bG;
+            bFx += -q * wg * ex * bG;
+            bFy += -q * wg * ey * bG;
+            // s_i = 3 c.u + 4.5 (c.u)^2 - 1.5 |u|^2   (Eq. 26)
+            bux += bs * (T(3) * T(cx) + T(9) * cu * T(cx) - T(3) * ux);
+            buy += bs * (T(3) * T(cy) + T(9) * cu * T(cy) - T(3) * uy);
+        }
+        W[B_P][k] = bp;
+        W[B_RHO][k] = brho;
+        W[B_PHI][k] = bphi;
+        W[B_MU][k] = bmu;
+        W[B_UX][k] = bux;
+        W[B_UY][k] = buy;
+        W[B_FX][k] = bFx;
+        W[B_FY][k] = bFy;
+        W[B_GRX][k] = bgrx;
+        W[B_GRY][k] = bgry;
+        W[B_LMU][k] = blm;
+        W[B_GPX][k] = bgpx;
+        W[B_GPY][k] = bgpy;
+        W[B_ALPHA][k] = balpha;
+        W[B_GL][k] = bgl;
+    }
+}
+
+// grad p transposed (extrapolated ghosts) gives the full adjoint of p; then
+// p, u, F backwards (Eqs. 31-32) and the f terms through sum f and j.
+template <class T>
+__global__ void k_adj_p(T *__restrict__ lam, const AdjP<T> P, AdjW<T> W) {
+    const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
+    const long long N = (long long)P.k.nx * P.k.ny, NS = P.k.NS;
+    const KP<T> &K = P.k;
+    const T *gbx = W[B_GPX], *gby = W[B_GPY];
+    ADJ_LOOP(k, N) {
+        const int y = (int)(k / B.nx), x = (int)(k - (long long)y * B.nx);
+        const T bp = W[B_P][k] + tgather(B, x, y, true, [&](long long c, int i, T coef) {
+                         return coef * T(3.0 * D2Q9::w(i)) *
+                                (T(D2Q9::cx(i)) * gbx[c] + T(D2Q9::cy(i)) * gby[c]);
+                     });
+        const T rho = W[A_RHO][k], phi = W[A_PHI][k], lm = W[A_LMU][k];
+        const T ux = W[A_UX][k], uy = W[A_UY][k];
+        const T gphx = W[A_GPHX][k], gphy = W[A_GPHY][k];
+        // p = sum f + (drho u.grad phi - gamma lambda rho lap mu) / 6
+        const T bux = W[B_UX][k] + K.drho / T(6) * gphx * bp;
+        const T buy = W[B_UY][k] + K.drho / T(6) * gphy * bp;
+        const T bgphx = K.drho / T(6) * ux * bp + K.drho * W[B_GRX][k];
+        const T bgphy = K.drho / T(6) * uy * bp + K.drho * W[B_GRY][k];
+        const T blm = W[B_LMU][k] - K.gl / T(6) * rho * bp;
+        T brho = W[B_RHO][k] - K.gl / T(6) * lm * bp;
+        W[B_GL][k] += -rho * lm / T(6) * bp;
+        // u = (j + F/6) 3 / rho
+        const T jx = T(3) / rho * bux, jy = T(3) / rho * buy;
+        const T bFx = W[B_FX][k] + bux / (T(2) * rho);
+        const T bFy = W[B_FY][k] + buy / (T(2) * rho);
+        brho += -(ux * bux + uy * buy) / rho;
+        // F = -phi grad mu + (0, -(rho - rho_ref) g)
+        brho += -K.grav * bFy;
+        W[B_PHI][k] += -(W[A_GMUX][k] * bFx + W[A_GMUY][k] * bFy);
+        W[B_GMUX][k] = -phi * bFx;
+        W[B_GMUY][k] = -phi * bFy;
+        W[B_GPHX][k] = bgphx;
+        W[B_GPHY][k] = bgphy;
+        W[B_LMU][k] = blm;
+        W[B_RHO][k] = brho;
+        // sum f and j feed every f_i
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            lam[i * NS + k] += bp + T(D2Q9::cx(i)) * jx + T(D2Q9::cy(i)) * jy;
+    }
+}
+
+// grad mu and lap mu transposed (mirror ghosts): full adjoint of mu; the
+// sigma term mu1 * mu_bar.
+template <class T>
+__global__ void k_adj_mu(const AdjP<T> P, AdjW<T> W) {
+    const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
+    const long long N = (long long)P.k.nx * P.k.ny;
+    const T *gx = W[B_GMUX], *gy = W[B_GMUY], *bl = W[B_LMU];
+    ADJ_LOOP(k, N) {
+        const int y = (int)(k / B.nx), x = (int)(k - (long long)y * B.nx);
+        const T t = tgather(B, x, y, false, [&](long long c, int i, T coef) {
+            return coef * (T(3.0 * D2Q9::w(i)) * (T(D2Q9::cx(i)) * gx[c] + T(D2Q9::cy(i)) * gy[c]) +
+                           T(6.0 * D2Q9::w(i)) * bl[c]);
+        });
+        const T bmu = W[B_MU][k] + t - T(10.0 / 3.0) * bl[k];
+        W[B_MU][k] = bmu;
+        W[B_SIGMA][k] = bmu * W[A_MU1][k];
+    }
+}
+
+// grad phi and lap phi transposed: full adjoint of phi, then phi = sum g.
+template <class T>
+__global__ void k_adj_phi(T *__restrict__ lam, const AdjP<T> P, AdjW<T> W) {
+    const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
+    const long long N = (long long)P.k.nx * P.k.ny, NS = P.k.NS;
+    const KP<T> &K = P.k;
+    const T *gx = W[B_GPHX], *gy = W[B_GPHY], *bm = W[B_MU];
+    ADJ_LOOP(k, N) {
+        const int y = (int)(k / B.nx), x = (int)(k - (long long)y * B.nx);
+        const T ph = W[A_PHI][k];
+        // psi''(phi) = 4 beta [(phi-a)(phi-b) + (phi-a)(phi-m) + (phi-b)(phi-m)]
+        const T a = ph - K.phiA, b = ph - K.phiB, m = ph - K.phibar;
+        const T psi2 = K.beta4 * (a * b + a * m + b * m);
+        const T t = tgather(B, x, y, false, [&](long long c, int i, T coef) {
+            return coef * (T(3.0 * D2Q9::w(i)) * (T(D2Q9::cx(i)) * gx[c] + T(D2Q9::cy(i)) * gy[c]) -
+                           K.kappa * T(6.0 * D2Q9::w(i)) * bm[c]);
+        });
+        const T bphi = W[B_PHI][k] + K.drho * W[B_RHO][k] + psi2 * bm[k] + t +
+                       K.kappa * T(10.0 / 3.0) * bm[k];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) lam[(9 + i) * NS + k] += bphi;
+    }
+}
+
+// Adjoint of the equilibrium initial state (u = 0: f = 0, g_0 = phi -
+// (1 - w_0) alpha mu, g_i = w_i alpha mu): mu_bar, alpha_bar and sigma_bar
+// per cell, from lambda_0 (g slots).
+template <class T>
+__global__ void k_adj_init_a(const T *__restrict__ lam0, const AdjP<T> P, AdjW<T> W) {
+    const long long N = (long long)P.k.nx * P.k.ny, NS = P.k.NS;
+    ADJ_LOOP(k, N) {
+        T br = -T(1.0 - D2Q9::w(0)) * lam0[9 * NS + k];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) br += T(D2Q9::w(i)) * lam0[(9 + i) * NS + k];
+        const T bmu = P.k.alpha * br;
+        W[B_MU][k] = bmu;
+        W[B_ALPHA][k] = W[A_MU][k] * br;
+        W[B_GL][k] = T(0);
+        W[B_SIGMA][k] = bmu * W[A_MU1][k];
+    }
+}
+
+// phi0_bar = lambda_0 g_0 + psi'' mu_bar - kappa lap^T mu_bar.
+template <class T>
+__global__ void k_adj_init_b(const T *__restrict__ lam0, T *__restrict__ phi0_bar, const AdjP<T> P,
+                             AdjW<T> W) {
+    const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
+    const long long N = (long long)P.k.nx * P.k.ny, NS = P.k.NS;
+    const KP<T> &K = P.k;
+    const T *bm = W[B_MU];
+    ADJ_LOOP(k, N) {
+        const int y = (int)(k / B.nx), x = (int)(k - (long long)y * B.nx);
+        const T ph = W[A_PHI][k];
+        const T a = ph - K.phiA, b = ph - K.phiB, m = ph - K.phibar;
+        const T psi2 = K.beta4 * (a * b + a * m + b * m);
+        const T t = tgather(B, x, y, false, [&](long long c, int i, T coef) {
+            return coef * (-K.kappa * T(6.0 * D2Q9::w(i)) * bm[c]);
+        });
+        phi0_bar[k] = lam0[9 * NS + k] + psi2 * bm[k] + t + K.kappa * T(10.0 / 3.0) * bm[k];
+    }
+}
+
+// Loss seed: lambda_T = dL/ds_T with L = sum (phi_T - target)^2; per-block
+// FP64 partial sums of the loss.
+template <class T>
+__global__ void __launch_bounds__(256)
+k_adj_seed(const T *__restrict__ lvl, const T *__restrict__ target, T *__restrict__ lam,
+           const AdjP<T> P, double *__restrict__ part) {
+    const long long N = (long long)P.k.nx * P.k.ny, NS = P.k.NS;
+    double acc = 0.0;
+    ADJ_LOOP(k, N) {
+        T phi = T(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) phi += lvl[(9 + i) * NS + k];
+        const T d = phi - target[k];
+        acc += (double)d * (double)d;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            lam[i * NS + k] = T(0);
+            lam[(9 + i) * NS + k] = T(2) * d;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __shared__ double wsum[8];
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int i = 0; i < 8; ++i) a += wsum[i];
+        part[blockIdx.x] = a;
+    }
+}
+
+// Per-block FP64 partial sums of the (M, sigma) terms of one reverse step:
+// dM = sum alpha1 alpha_bar + gamma (gamma lambda)_bar, dsigma = sum sigma_bar.
+template <class T>
+__global__ void __launch_bounds__(256)
+k_adj_theta(const AdjP<T> P, AdjW<T> W, double *__restrict__ part) {
+    const long long N = (long long)P.k.nx * P.k.ny;
+    double dM = 0.0, dS = 0.0;
+    const double a1 = (double)P.alpha1, gm = (double)P.gamma;
+    ADJ_LOOP(k, N) {
+        dM += a1 * (double)W[B_ALPHA][k] + gm * (double)W[B_GL][k];
+        dS += (double)W[B_SIGMA][k];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dM += __shfl_down_sync(0xffffffffu, dM, o);
+        dS += __shfl_down_sync(0xffffffffu, dS, o);
+    }
+    __shared__ double wm[8], ws[8];
+    if ((threadIdx.x & 31) == 0) {
+        wm[threadIdx.x >> 5] = dM;
+        ws[threadIdx.x >> 5] = dS;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < 8; ++i) {
+            a += wm[i];
+            b += ws[i];
+        }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+// Adds the per-block partials, in block order, to the running totals.
+static __global__ void k_adj_accumulate(const double *__restrict__ part, int nblocks, int width,
+                                        double *__restrict__ acc) {
+    if (threadIdx.x < width) {
+        double a = 0.0;
+        for (int b = 0; b < nblocks; ++b) a += part[width * b + threadIdx.x];
+        acc[threadIdx.x] += a;
+    }
+}
+
+}  // namespace lbm

@@ -104,6 +104,19 @@ Layout layout(const Derived &d, const Ops *ops) {
 
 void lbm_internal_set_error(const char *msg) { g_create_err = msg ? msg : ""; }
 
+namespace lbm {
+// Adjoint work buffer: A_COUNT field arrays of NS elements, then the
+// per-block partials, then 4 doubles (dM, dsigma totals, loss, spare).
+constexpr int kAdjArrays = 36;
+size_t adj_part_offset(long long NS, size_t elem) {
+    return round256((size_t)kAdjArrays * (size_t)NS * elem);
+}
+size_t adj_acc_offset(long long NS, size_t elem) {
+    return adj_part_offset(NS, elem) + round256((size_t)kAdjBlocks * 2 * sizeof(double));
+}
+size_t adj_work_bytes(long long NS, size_t elem) { return adj_acc_offset(NS, elem) + 256; }
+}  // namespace lbm
+
 struct lbm_sim {
     lbm_params prm;
     Derived d;
@@ -333,5 +346,82 @@ const char *lbm_last_error(const lbm_sim *s) { return s ? s->err.c_str() : "null
 const char *lbm_create_error(void) { return g_create_err.c_str(); }
 
 void lbm_destroy(lbm_sim *s) { delete s; }
+
+// ------------------------------------------------------------- adjoint
+
+static lbm::AdjHost adj_host(const lbm_params &p) {
+    lbm::AdjHost h;
+    const double d = p.phi_A - p.phi_B;
+    h.alpha1 = 1.0 / ((p.tau_g - 0.5) / 3.0);
+    h.gamma = (p.rho_A - p.rho_B) / (p.rho_B * p.phi_A - p.rho_A * p.phi_B);
+    h.kappa1 = 3.0 * p.W / (2.0 * d * d);
+    h.beta1 = 12.0 / (p.W * d * d * d * d);
+    return h;
+}
+
+static lbm_status adj_ready(lbm_sim *s, const void *work) {
+    if (!s) return LBM_ERR_ARG;
+    if (!s->ops->adj_step) return s->fail(LBM_ERR_ARG, "the adjoint needs LBM_F64 or LBM_F32");
+    if (!work) return s->fail(LBM_ERR_ARG, "null adjoint work buffer");
+    if (reinterpret_cast<uintptr_t>(work) & 255)
+        return s->fail(LBM_ERR_ARG, "adjoint work buffer must be 256-byte aligned");
+    return LBM_OK;
+}
+
+lbm_status lbm_adj_work_bytes(const lbm_sim *s, size_t *bytes) {
+    if (!s || !bytes) return LBM_ERR_ARG;
+    if (!s->ops->adj_step) return LBM_ERR_ARG;
+    *bytes = lbm::adj_work_bytes(s->d.NS, s->ops->field_size);
+    return LBM_OK;
+}
+
+lbm_status lbm_adj_reset(lbm_sim *s, void *work) {
+    if (lbm_status st = adj_ready(s, work)) return st;
+    char *acc = static_cast<char *>(work) + lbm::adj_acc_offset(s->d.NS, s->ops->field_size);
+    LBM_CK(s, cudaMemsetAsync(acc, 0, 4 * sizeof(double), s->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_adj_seed(lbm_sim *s, const void *state_T, const void *phi_target, void *lam_T,
+                        void *work, double *loss) {
+    if (lbm_status st = adj_ready(s, work)) return st;
+    if (!state_T || !phi_target || !lam_T) return s->fail(LBM_ERR_ARG, "null pointer");
+    LBM_CK(s, s->ops->adj_seed(s->d, adj_host(s->prm), state_T, phi_target, lam_T, work, s->stream));
+    if (loss) {
+        const char *acc = static_cast<const char *>(work) + lbm::adj_acc_offset(s->d.NS, s->ops->field_size);
+        LBM_CK(s, cudaMemcpyAsync(loss, acc + 2 * sizeof(double), sizeof(double),
+                                  cudaMemcpyDeviceToHost, s->stream));
+        LBM_CK(s, cudaStreamSynchronize(s->stream));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_adj_step(lbm_sim *s, const void *state_t, const void *lam_next, void *lam_t,
+                        void *work) {
+    if (lbm_status st = adj_ready(s, work)) return st;
+    if (!state_t || !lam_next || !lam_t) return s->fail(LBM_ERR_ARG, "null pointer");
+    if (lam_next == lam_t) return s->fail(LBM_ERR_ARG, "lam_next and lam_t must differ");
+    LBM_CK(s, s->ops->adj_step(s->d, adj_host(s->prm), state_t, lam_next, lam_t, work, s->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_adj_init(lbm_sim *s, const void *phi0, const void *lam_0, void *phi0_bar,
+                        void *work) {
+    if (lbm_status st = adj_ready(s, work)) return st;
+    if (!phi0 || !lam_0 || !phi0_bar) return s->fail(LBM_ERR_ARG, "null pointer");
+    LBM_CK(s, s->ops->adj_init(s->d, adj_host(s->prm), phi0, lam_0, phi0_bar, work, s->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_adj_grads(lbm_sim *s, void *work, double *dM, double *dsigma) {
+    if (lbm_status st = adj_ready(s, work)) return st;
+    double h[2];
+    const char *acc = static_cast<const char *>(work) + lbm::adj_acc_offset(s->d.NS, s->ops->field_size);
+    LBM_CK(s, cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+    LBM_CK(s, cudaStreamSynchronize(s->stream));
+    if (dM) *dM = h[0];
+    if (dsigma) *dsigma = h[1];
+    return LBM_OK;
+}
 
 }  // extern "C"

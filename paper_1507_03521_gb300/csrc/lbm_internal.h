@@ -16,6 +16,21 @@ struct Derived {
     double grav, rhoref, tau_f, tau_g, uwb, uwt;
 };
 
+// Extra constants of the adjoint: derivatives of the model constants with
+// respect to M and sigma.
+struct AdjHost {
+    double alpha1;  // alpha per unit M
+    double gamma;   // gamma lambda per unit M
+    double kappa1, beta1;  // kappa, beta per unit sigma
+};
+
+// Work-buffer layout of the adjoint: arrays, per-block partials, running
+// (dM, dsigma) totals and the loss.
+constexpr int kAdjBlocks = 152 * 4;
+size_t adj_work_bytes(long long NS, size_t elem);
+size_t adj_part_offset(long long NS, size_t elem);
+size_t adj_acc_offset(long long NS, size_t elem);
+
 // One work item of the batched strip form (see lbm_strip.cuh).
 struct BatchItem {
     int dom, x0, ys, ye;
@@ -45,6 +60,13 @@ struct Ops {
     cudaError_t (*batch_slots)(int *slots);  // resident CTAs of one batch launch
     cudaError_t (*batch_step)(char *state, const void *doms, const BatchItem *items, int nitems,
                               int parity, int grid, cudaStream_t s);
+    // adjoint (plain FP64 / FP32 storage only; null otherwise)
+    cudaError_t (*adj_seed)(const Derived &, const AdjHost &, const void *lvl, const void *target,
+                            void *lam, void *work, cudaStream_t s);
+    cudaError_t (*adj_step)(const Derived &, const AdjHost &, const void *lvl,
+                            const void *lam_next, void *lam, void *work, cudaStream_t s);
+    cudaError_t (*adj_init)(const Derived &, const AdjHost &, const void *phi0, const void *lam0,
+                            void *phi0_bar, void *work, cudaStream_t s);
 };
 
 const Ops *ops_f64();

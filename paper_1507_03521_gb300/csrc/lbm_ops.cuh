@@ -2,7 +2,10 @@
 // (compute type, storage type, tile height) choice.
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_internal.h"
+#include "lbm_adjoint.cuh"
 #include "lbm_kernels.cuh"
 #include "lbm_strip.cuh"
 
@@ -208,11 +211,84 @@ struct OpsImpl {
         return cudaGetLastError();
     }
 
+    // ---- adjoint (plain storage only)
+    static constexpr bool kPlain = std::is_same<ST, PlainStore<T>>::value;
+
+    static AdjP<T> make_ap(const Derived &d, const AdjHost &h) {
+        AdjP<T> a;
+        a.k = make_kp<T>(d);
+        a.alpha1 = T(h.alpha1);
+        a.gamma = T(h.gamma);
+        a.kappa1 = T(h.kappa1);
+        a.beta1 = T(h.beta1);
+        return a;
+    }
+    static AdjW<T> make_w(const Derived &d, void *work) {
+        return AdjW<T>{static_cast<T *>(work), d.NS};
+    }
+    static int adj_grid(const Derived &d) {
+        long long nb = (d.N + 255) / 256;
+        return (int)(nb < kAdjBlocks ? nb : kAdjBlocks);
+    }
+    static double *part(const Derived &d, void *work) {
+        return reinterpret_cast<double *>(static_cast<char *>(work) +
+                                          adj_part_offset(d.NS, sizeof(T)));
+    }
+    static double *acc(const Derived &d, void *work) {
+        return reinterpret_cast<double *>(static_cast<char *>(work) +
+                                          adj_acc_offset(d.NS, sizeof(T)));
+    }
+
+    static cudaError_t adj_seed(const Derived &d, const AdjHost &h, const void *lvl,
+                                const void *target, void *lam, void *work, cudaStream_t s) {
+        const int nb = adj_grid(d);
+        k_adj_seed<T><<<nb, 256, 0, s>>>(static_cast<const T *>(lvl), static_cast<const T *>(target),
+                                         static_cast<T *>(lam), make_ap(d, h), part(d, work));
+        k_reduce_final<<<1, 32, 0, s>>>(part(d, work), nb, 1, acc(d, work) + 2);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t adj_step(const Derived &d, const AdjHost &h, const void *lvl,
+                                const void *lam_next, void *lam, void *work, cudaStream_t s) {
+        const AdjP<T> P = make_ap(d, h);
+        const AdjW<T> W = make_w(d, work);
+        const int nb = adj_grid(d);
+        T *L = static_cast<T *>(lam);
+        k_adj_f0<T><<<nb, 256, 0, s>>>(static_cast<const T *>(lvl), P, W);
+        k_adj_f1<T><<<nb, 256, 0, s>>>(P, W);
+        k_adj_f2<T><<<nb, 256, 0, s>>>(P, W);
+        k_adj_f3<T><<<nb, 256, 0, s>>>(P, W);
+        k_adj_collide<T><<<nb, 256, 0, s>>>(static_cast<const T *>(lam_next), L, P, W);
+        k_adj_p<T><<<nb, 256, 0, s>>>(L, P, W);
+        k_adj_mu<T><<<nb, 256, 0, s>>>(P, W);
+        k_adj_phi<T><<<nb, 256, 0, s>>>(L, P, W);
+        k_adj_theta<T><<<nb, 256, 0, s>>>(P, W, part(d, work));
+        k_adj_accumulate<<<1, 32, 0, s>>>(part(d, work), nb, 2, acc(d, work));
+        return cudaGetLastError();
+    }
+
+    static cudaError_t adj_init(const Derived &d, const AdjHost &h, const void *phi0,
+                                const void *lam0, void *phi0_bar, void *work, cudaStream_t s) {
+        const AdjP<T> P = make_ap(d, h);
+        const AdjW<T> W = make_w(d, work);
+        const int nb = adj_grid(d);
+        k_adj_phi0<T><<<nb, 256, 0, s>>>(static_cast<const T *>(phi0), P, W);
+        k_adj_f1<T><<<nb, 256, 0, s>>>(P, W);
+        k_adj_init_a<T><<<nb, 256, 0, s>>>(static_cast<const T *>(lam0), P, W);
+        k_adj_init_b<T><<<nb, 256, 0, s>>>(static_cast<const T *>(lam0), static_cast<T *>(phi0_bar),
+                                           P, W);
+        k_adj_theta<T><<<nb, 256, 0, s>>>(P, W, part(d, work));
+        k_adj_accumulate<<<1, 32, 0, s>>>(part(d, work), nb, 2, acc(d, work));
+        return cudaGetLastError();
+    }
+
     static const Ops *ops(const char *name) {
         static const Ops o = {name,           sizeof(T),      &level_bytes,      &step,
                               &fields,        &init,          &mass,             &laplace,
                               SW,             &strip_ok,      sizeof(BatchDom<T>), &batch_fill_dom,
-                              &batch_slots,   &batch_step};
+                              &batch_slots,   &batch_step,
+                              kPlain ? &adj_seed : nullptr, kPlain ? &adj_step : nullptr,
+                              kPlain ? &adj_init : nullptr};
         return &o;
     }
 };

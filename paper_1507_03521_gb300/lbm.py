@@ -32,7 +32,8 @@ EXPORTS = ["lbm_version", "lbm_buffer_sizes", "lbm_create", "lbm_bind_buffers", 
            "lbm_batch_init_phi", "lbm_batch_step", "lbm_batch_set_graph", "lbm_batch_set_segment",
            "lbm_batch_autotune", "lbm_batch_fields", "lbm_batch_mass", "lbm_batch_cells",
            "lbm_batch_step_count", "lbm_batch_segment", "lbm_batch_last_error",
-           "lbm_batch_destroy"]
+           "lbm_batch_destroy", "lbm_adj_work_bytes", "lbm_adj_reset", "lbm_adj_seed",
+           "lbm_adj_step", "lbm_adj_init", "lbm_adj_grads"]
 
 
 class LBMError(RuntimeError):
@@ -136,6 +137,18 @@ def load(path: str = LIB_PATH):
     lib.lbm_batch_last_error.argtypes = [_vp]
     lib.lbm_batch_destroy.restype = None
     lib.lbm_batch_destroy.argtypes = [_vp]
+    lib.lbm_adj_work_bytes.restype = S
+    lib.lbm_adj_work_bytes.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.lbm_adj_reset.restype = S
+    lib.lbm_adj_reset.argtypes = [_vp, _vp]
+    lib.lbm_adj_seed.restype = S
+    lib.lbm_adj_seed.argtypes = [_vp, _vp, _vp, _vp, _vp, _dp]
+    lib.lbm_adj_step.restype = S
+    lib.lbm_adj_step.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    lib.lbm_adj_init.restype = S
+    lib.lbm_adj_init.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    lib.lbm_adj_grads.restype = S
+    lib.lbm_adj_grads.argtypes = [_vp, _vp, _dp, _dp]
     _lib = lib
     return lib
 
@@ -281,6 +294,41 @@ class Sim:
 
     def set_state(self, buf, step: int):
         self._check(self._lib.lbm_set_state(self._h, buf.data_ptr(), 0, int(step)))
+
+    # -- adjoint (f64 / f32 handles)
+    def adj_work(self):
+        import torch
+        b = ctypes.c_size_t()
+        self._check(self._lib.lbm_adj_work_bytes(self._h, ctypes.byref(b)))
+        w = torch.empty(b.value, dtype=torch.uint8, device=self.device)
+        self._check(self._lib.lbm_adj_reset(self._h, w.data_ptr()))
+        return w
+
+    def adj_seed(self, state, target, lam, work):
+        t = self._field_tensor(target)
+        self._keep_target = t
+        loss = ctypes.c_double()
+        self._check(self._lib.lbm_adj_seed(self._h, state.data_ptr(), t.data_ptr(),
+                                           lam.data_ptr(), work.data_ptr(), ctypes.byref(loss)))
+        return loss.value
+
+    def adj_step(self, state, lam_next, lam, work):
+        self._check(self._lib.lbm_adj_step(self._h, state.data_ptr(), lam_next.data_ptr(),
+                                           lam.data_ptr(), work.data_ptr()))
+
+    def adj_init(self, phi0, lam0, work):
+        import torch
+        ph = self._field_tensor(phi0)
+        out = torch.empty(self.shape, dtype=self.field_dtype, device=self.device)
+        self._check(self._lib.lbm_adj_init(self._h, ph.data_ptr(), lam0.data_ptr(),
+                                           out.data_ptr(), work.data_ptr()))
+        return out
+
+    def adj_grads(self, work):
+        dM, dS = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.lbm_adj_grads(self._h, work.data_ptr(), ctypes.byref(dM),
+                                            ctypes.byref(dS)))
+        return dM.value, dS.value
 
 
 class Batch:

@@ -206,3 +206,15 @@ def batch_domains(n=1024, seed=1507036, sides=tuple(range(64, 513, 32)), max_sid
             phi = layer_field(nx, ny, ny / 4.0, 3.0 * ny / 4.0 - 1.0, 4.0, 1.0, -1.0)
         out.append((p, phi))
     return out
+
+
+def shear_droplet(n=512, R=64.0, u_wall=0.01, rho_ratio=10.0):
+    """Droplet in shear: n x n, centred droplet of radius R (W = 4), walls at
+    y = -1/2 and n - 1/2 moving at -u_wall (bottom) and +u_wall (top),
+    rho_A/rho_B = rho_ratio, sigma = 1e-3, M = 0.05, tau_f = tau_g = 0.8,
+    periodic in x."""
+    p = _base(nx=n, ny=n, rho_A=1.0, rho_B=1.0 / rho_ratio, sigma=1e-3, W=4.0, M=0.05,
+              tau_f=0.8, tau_g=0.8, bc_y=WALL, u_wall_bottom=-u_wall, u_wall_top=u_wall,
+              rho_ref=1.0)
+    phi = droplet_field(n, n, n / 2.0, n / 2.0, R, 4.0, 1.0, -1.0, periodic=False)
+    return p, phi

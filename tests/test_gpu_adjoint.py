@@ -1,0 +1,167 @@
+"""The hand-written adjoint (lbm_adj_*) against autograd through the plain
+PyTorch step, central finite differences of the CUDA forward, and itself
+under different checkpoint intervals."""
+import numpy as np
+import pytest
+import torch
+
+from oracle.torch_step import TorchStep
+from paper_1507_03521_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1507_03521_gb300 import build, lbm
+    build.build()
+    return lbm
+
+
+def _state_pops(buf, N, dtype=np.float64):
+    NS = (N + 127) // 128 * 128
+    return buf.cpu().numpy().view(dtype).reshape(18, NS)[:, :N]
+
+
+def _to_state(pops18, N, device):
+    NS = (N + 127) // 128 * 128
+    a = np.zeros((18, NS))
+    a[:, :N] = pops18
+    return torch.from_numpy(a.ravel().copy()).view(torch.uint8).to(device)
+
+
+CASES = [
+    ("periodic13x11", dict(walls=False)),
+    ("walls12x9", dict(walls=True, gravity=2e-5, u_wall=0.02)),
+    ("walls16x16", dict(walls=True, gravity=-1e-5, u_wall=-0.01)),
+]
+
+
+@pytest.mark.parametrize("name,kw", CASES, ids=[c[0] for c in CASES])
+def test_one_step_vjp_matches_autograd(L, name, kw):
+    """lambda_t = (ds_{t+1}/ds_t)^T lambda_{t+1} and the (M, sigma) terms,
+    for a random state and a random lambda_{t+1}, element by element."""
+    nx, ny = {"periodic13x11": (13, 11), "walls12x9": (12, 9), "walls16x16": (16, 16)}[name]
+    p, phi, ux, uy = W.small_case(nx, ny, seed=31, **kw)
+    N = nx * ny
+    # a state s_t: a few forward steps from the seeded initial state
+    sim = L.Sim(p, "f64")
+    sim.init_phi(phi, ux, uy)
+    sim.step(4)
+    st, _ = sim.get_state()
+    pops = _state_pops(st, N)
+    rng = np.random.default_rng(5)
+    lam1 = rng.standard_normal((18, N))
+    work = sim.adj_work()
+    lam_out = torch.empty_like(st)
+    sim.adj_step(st, _to_state(lam1, N, st.device), lam_out, work)
+    got = _state_pops(lam_out, N)
+    dM, dS = sim.adj_grads(work)
+    # reference: autograd VJP of the PyTorch step
+    ts = TorchStep(p)
+    f = torch.from_numpy(pops[:9].reshape(9, ny, nx).copy()).requires_grad_(True)
+    g = torch.from_numpy(pops[9:].reshape(9, ny, nx).copy()).requires_grad_(True)
+    M = torch.tensor(p["M"], dtype=torch.float64, requires_grad=True)
+    sg = torch.tensor(p["sigma"], dtype=torch.float64, requires_grad=True)
+    f1, g1 = ts.step(f, g, M, sg)
+    lt = torch.from_numpy(lam1.reshape(18, ny, nx))
+    (f1 * lt[:9]).sum().add((g1 * lt[9:]).sum()).backward()
+    ref = np.concatenate([f.grad.numpy().reshape(9, N), g.grad.numpy().reshape(9, N)])
+    assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+    assert dM == pytest.approx(M.grad.item(), rel=1e-10, abs=1e-14)
+    assert dS == pytest.approx(sg.grad.item(), rel=1e-10, abs=1e-14)
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_rollout_gradients_match_autograd(L, walls):
+    """dL/dphi0, dL/dM, dL/dsigma through 6 steps and the initial state."""
+    from paper_1507_03521_gb300.adjoint import rollout_loss
+    p, phi, _, _ = W.small_case(16, 12, seed=32, walls=walls, gravity=1e-5, u_wall=0.01)
+    target = np.roll(phi, 2, axis=1)
+    ph = torch.from_numpy(phi).clone().requires_grad_(True)
+    M = torch.tensor(p["M"], dtype=torch.float64, requires_grad=True)
+    sg = torch.tensor(p["sigma"], dtype=torch.float64, requires_grad=True)
+    loss = rollout_loss(ph, M, sg, p, 6, torch.from_numpy(target), K=4, dtype="f64")
+    loss.backward()
+    ts = TorchStep(p)
+    ph2 = torch.from_numpy(phi).clone().requires_grad_(True)
+    M2 = torch.tensor(p["M"], dtype=torch.float64, requires_grad=True)
+    s2 = torch.tensor(p["sigma"], dtype=torch.float64, requires_grad=True)
+    ref = ts.rollout_loss(ph2, M2, s2, 6, torch.from_numpy(target))
+    ref.backward()
+    assert loss.item() == pytest.approx(ref.item(), rel=1e-12)
+    assert np.abs(ph.grad.numpy() - ph2.grad.numpy()).max() <= 1e-10 * np.abs(ph2.grad.numpy()).max()
+    assert M.grad.item() == pytest.approx(M2.grad.item(), rel=1e-9)
+    assert sg.grad.item() == pytest.approx(s2.grad.item(), rel=1e-9)
+
+
+def test_gradients_match_finite_differences(L):
+    """Droplet in shear at 64 x 64 (R = 8, walls moving at +-0.01, rho
+    ratio 10), 200 steps, FP64: central differences of the CUDA forward with
+    relative step 1e-4 against the adjoint."""
+    from paper_1507_03521_gb300.adjoint import rollout_loss
+    p, phi = W.shear_droplet(n=64, R=8.0)
+    pt = dict(p, M=1.05 * p["M"], sigma=0.95 * p["sigma"])
+    target = _forward_phi(L, pt, phi, 200)
+    tgt = torch.from_numpy(target)
+    ph = torch.from_numpy(phi).clone().requires_grad_(True)
+    M = torch.tensor(p["M"], dtype=torch.float64, requires_grad=True)
+    sg = torch.tensor(p["sigma"], dtype=torch.float64, requires_grad=True)
+    loss = rollout_loss(ph, M, sg, p, 200, tgt, K=50, dtype="f64")
+    loss.backward()
+
+    def Lval(phi_, M_, s_):
+        out = _forward_phi(L, dict(p, M=M_, sigma=s_), phi_, 200)
+        return float(((out - target) ** 2).sum())
+
+    h = 1e-4
+    fdM = (Lval(phi, p["M"] * (1 + h), p["sigma"]) - Lval(phi, p["M"] * (1 - h), p["sigma"])) / (2 * h * p["M"])
+    fdS = (Lval(phi, p["M"], p["sigma"] * (1 + h)) - Lval(phi, p["M"], p["sigma"] * (1 - h))) / (2 * h * p["sigma"])
+    v = np.random.default_rng(3).standard_normal(phi.shape) * 1e-2
+    fdP = (Lval(phi + h * v, p["M"], p["sigma"]) - Lval(phi - h * v, p["M"], p["sigma"])) / (2 * h)
+    assert M.grad.item() == pytest.approx(fdM, rel=1e-5)
+    assert sg.grad.item() == pytest.approx(fdS, rel=1e-5)
+    assert float((ph.grad.numpy() * v).sum()) == pytest.approx(fdP, rel=1e-5)
+
+
+def _forward_phi(L, p, phi, steps):
+    s = L.Sim(p, "f64")
+    s.init_phi(phi)
+    s.step(steps)
+    out = s.fields(("phi",))["phi"].cpu().numpy()
+    s.close()
+    return out
+
+
+def test_checkpoint_interval_does_not_change_gradients(L):
+    from paper_1507_03521_gb300.adjoint import rollout_loss
+    p, phi = W.shear_droplet(n=32, R=6.0)
+    tgt = torch.from_numpy(np.roll(phi, 1, axis=0))
+    res = []
+    for K in (1, 7, 1000):
+        ph = torch.from_numpy(phi).clone().requires_grad_(True)
+        M = torch.tensor(p["M"], dtype=torch.float64, requires_grad=True)
+        sg = torch.tensor(p["sigma"], dtype=torch.float64, requires_grad=True)
+        rollout_loss(ph, M, sg, p, 30, tgt, K=K).backward()
+        res.append((ph.grad.numpy().copy(), M.grad.item(), sg.grad.item()))
+    for r in res[1:]:
+        assert np.array_equal(r[0], res[0][0]) and r[1] == res[0][1] and r[2] == res[0][2]
+
+
+def test_f32_adjoint_close_to_f64(L):
+    from paper_1507_03521_gb300.adjoint import rollout_loss
+    p, phi = W.shear_droplet(n=32, R=6.0)
+    tgt = torch.from_numpy(np.roll(phi, 1, axis=0))
+    out = {}
+    for dt in ("f64", "f32"):
+        ph = torch.from_numpy(phi).clone().requires_grad_(True)
+        M = torch.tensor(p["M"], dtype=torch.float64, requires_grad=True)
+        sg = torch.tensor(p["sigma"], dtype=torch.float64, requires_grad=True)
+        rollout_loss(ph, M, sg, p, 40, tgt, K=10, dtype=dt).backward()
+        out[dt] = (ph.grad.numpy().astype(np.float64), M.grad.item(), sg.grad.item())
+    g64, g32 = out["f64"], out["f32"]
+    assert np.abs(g32[0] - g64[0]).max() <= 1e-3 * np.abs(g64[0]).max()
+    assert g32[1] == pytest.approx(g64[1], rel=1e-3)
+    assert g32[2] == pytest.approx(g64[2], rel=1e-3)
