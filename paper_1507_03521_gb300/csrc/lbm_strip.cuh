@@ -6,14 +6,14 @@
 // an x-halo only:
 //   * A CTA of SW threads owns a column strip x0 .. x0+SW-1 and a segment
 //     of rows ys .. ye-1, and marches up through y.  Iteration y
-//       1. phi       at row y+3 from the g populations of that row,
-//       2. sum f, j  at row y+1 from the f populations of that row,
-//       3. mu        at row y+2 (Eq. 5),
-//       4. u, p, F, lap mu, grad phi at row y+1 (Eqs. 31-32),
+//       1. phi at row y+3 from the g populations of that row,
+//       3. mu  at row y+2 (Eq. 5),
+//       4. p   at row y+1 (Eq. 32) from sum f and j of that row's f
+//          populations; each thread keeps u (Eq. 31), F, lap mu and
+//          grad phi of its own column in registers for the next iteration,
 //       5. collides row y (Eqs. 22-29) and pushes it to the other level.
-//     Rows of phi, mu, p and u live in small shared-memory rings.  The
-//     halo columns of steps 1-4 are spread over different warps so that no
-//     warp carries all the extra passes into the next barrier.
+//     Rows of phi, mu and p live in small shared-memory rings (4, 3, 3
+//     rows: the rows live at iteration y).
 //   * Population rows are copied global -> shared with cp.async (16-byte
 //     chunks, L2 only) DEPTH rows ahead of use, so DRAM traffic overlaps the
 //     arithmetic of the rows in flight.  Every population is read from DRAM
@@ -245,34 +245,23 @@ struct StripSmem {
     // g rows are read 3 iterations after they arrive (phi, then collision),
     // f rows 1 iteration after (sum f and j, then collision): separate rings.
     static constexpr int NBG = DEPTH + 4, NBF = DEPTH + 2;
-    static constexpr int RPHI = 5, RMU = 4, RP = 3, RU = 2;
+    // rows live at iteration y: phi y..y+3, mu y..y+2, p y-1..y+1
+    static constexpr int RPHI = 4, RMU = 3, RP = 3;
     static constexpr int WPHI = SW + 6, WMU = SW + 4, WQ = SW + 2;
     static constexpr size_t gb = (SR::gbytes + 15) / 16 * 16;
     static constexpr size_t fb = (SR::fbytes + 15) / 16 * 16;
     static constexpr size_t pop_bytes = gb * NBG + fb * NBF;
-    // fields: phi ring, mu ring, p ring, ps/jx/jy (1 row), and a 2-row ring
-    // of ux, uy, Fx, Fy, lap mu, grad phi (x, y)
     static constexpr size_t fld_elems =
-        (size_t)RPHI * WPHI + (size_t)RMU * WMU + (size_t)RP * WQ + 3 * (size_t)WQ + 7 * RU * (size_t)WQ;
+        (size_t)RPHI * WPHI + (size_t)RMU * WMU + (size_t)RP * WQ;
     static constexpr size_t bytes = pop_bytes + fld_elems * sizeof(T);
 
     char *pop;
-    T *phi, *mu, *p, *ps, *jx, *jy, *ux, *uy, *Fx, *Fy, *lmu, *gphx, *gphy;
+    T *phi, *mu, *p;
     __device__ __forceinline__ StripSmem(char *base) {
         pop = base;
         phi = reinterpret_cast<T *>(base + pop_bytes);
         mu = phi + RPHI * WPHI;
         p = mu + RMU * WMU;
-        ps = p + RP * WQ;
-        jx = ps + WQ;
-        jy = jx + WQ;
-        ux = jy + WQ;
-        uy = ux + RU * WQ;
-        Fx = uy + RU * WQ;
-        Fy = Fx + RU * WQ;
-        lmu = Fy + RU * WQ;
-        gphx = lmu + RU * WQ;
-        gphy = gphx + RU * WQ;
     }
     __device__ __forceinline__ char *gbuf(int row) const { return pop + (size_t)((row + 64) % NBG) * gb; }
     __device__ __forceinline__ char *fbuf(int row) const {
@@ -282,7 +271,6 @@ struct StripSmem {
     __device__ __forceinline__ T *phir(int row) const { return phi + ((row + 64) % RPHI) * WPHI + 3; }
     __device__ __forceinline__ T *mur(int row) const { return mu + ((row + 64) % RMU) * WMU + 2; }
     __device__ __forceinline__ T *pr(int row) const { return p + ((row + 64) % RP) * WQ + 1; }
-    __device__ __forceinline__ int ur(int row) const { return ((row + 64) % RU) * WQ + 1; }
 };
 
 // Column loop of one step: columns -h .. SW+h-1.  Every thread takes column
@@ -330,6 +318,10 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     // or bounce in y.
     const bool x_inner = x0 > 0 && x0 + SW < nx;
     const T c3 = T(1.0 / 3.0), c6 = T(0.5 / 3.0);
+    // u, F, lap mu, grad phi of column t: c_* at row y (from the previous
+    // iteration), n_* at row y+1 (computed in step 4 of this iteration)
+    T c_ux = 0, c_uy = 0, c_Fx = 0, c_Fy = 0, c_lm = 0, c_gx = 0, c_gy = 0;
+    T n_ux = 0, n_uy = 0, n_Fx = 0, n_Fy = 0, n_lm = 0, n_gx = 0, n_gy = 0;
 
     for (int y = yfirst; y < ye; ++y) {
         cp_async_wait<DEPTH - 1>();   // g row y+3, f row y+1 have landed (own chunks)
@@ -344,17 +336,6 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
                 T g[9];
                 SR::read_g(b, c + HP, g);
                 ph[c] = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-            });
-        }
-        // 2. sum f and j at row y+1, columns -1 .. SW
-        {
-            const char *b = s.fbuf(y + 1);
-            columns<SW, 1, 2>(t, [&](int c) {
-                T f[9];
-                SR::read_f(b, c + HP, f);
-                s.ps[c + 1] = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-                s.jx[c + 1] = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-                s.jy[c + 1] = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
             });
         }
         __syncthreads();
@@ -386,15 +367,23 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
         }
         __syncthreads();
 
-        // 4. u, p, F, lap mu, grad phi at row y+1, columns -1 .. SW
+        // 4. p at row y+1, columns -1 .. SW (Eq. 32), from sum f and j of
+        //    that row and phi, mu around it; thread t also keeps u, F,
+        //    lap mu and grad phi of its own column t for the next
+        //    iteration's collision (Eq. 31), in registers.
         {
             const int r = y + 1;
             T *po = s.pr(r);
-            const int uo = s.ur(r);
             if (!wall || (r >= 0 && r < ny)) {
                 const T *pu = s.phir(r + 1), *pc = s.phir(r), *pd = s.phir(r - 1);
                 const T *mu_ = s.mur(r + 1), *mc = s.mur(r), *md = s.mur(r - 1);
-                columns<SW, 1, 0>(t, [&](int c) {
+                const char *fbr = s.fbuf(r);
+                auto point = [&](int c, bool keep) {
+                    T f[9];
+                    SR::read_f(fbr, c + HP, f);
+                    const T sf = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+                    const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+                    const T jy = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
                     const T phi = pc[c];
                     const T pul = pu[c - 1], pur = pu[c + 1], pdl = pd[c - 1], pdr = pd[c + 1];
                     const T gphx = T(1.0 / 3.0) * (pc[c + 1] - pc[c - 1]) +
@@ -412,18 +401,23 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
                     const T Fx = -phi * gmx;
                     const T Fy = -phi * gmy - (rho - P.rhoref) * P.grav;
                     const T irc = T(3) * rcp_fast(rho);
-                    const T ux = (s.jx[c + 1] + c6 * Fx) * irc;
-                    const T uy = (s.jy[c + 1] + c6 * Fy) * irc;
+                    const T ux = (jx + c6 * Fx) * irc;
+                    const T uy = (jy + c6 * Fy) * irc;
                     const T udr = (ux * gphx + uy * gphy) * P.drho;
-                    po[c] = s.ps[c + 1] + c6 * (udr - P.gl * rho * lm);
-                    s.ux[uo + c] = ux;
-                    s.uy[uo + c] = uy;
-                    s.Fx[uo + c] = Fx;
-                    s.Fy[uo + c] = Fy;
-                    s.lmu[uo + c] = lm;
-                    s.gphx[uo + c] = gphx;
-                    s.gphy[uo + c] = gphy;
-                });
+                    po[c] = sf + c6 * (udr - P.gl * rho * lm);
+                    if (keep) {
+                        n_ux = ux;
+                        n_uy = uy;
+                        n_Fx = Fx;
+                        n_Fy = Fy;
+                        n_lm = lm;
+                        n_gx = gphx;
+                        n_gy = gphy;
+                    }
+                };
+                if (t < SW) point(t, true);
+                // halo columns -1 and SW: two lanes of the last warp
+                if (t >= SW - 32 && t < SW - 30) point(t == SW - 32 ? -1 : SW, false);
             } else if (r == ny) {
                 // ghost row above the top wall: linear extrapolation of p
                 const T *p1 = s.pr(ny - 1), *p2 = s.pr(ny - 2);
@@ -437,7 +431,6 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
             const int c = t;
             const int gx = x0 + c;
             if (gx < nx) {
-                const int uo = s.ur(y);
                 const T *pc = s.pr(y), *pu = s.pr(y + 1), *pd = s.pr(y - 1);
                 const bool lowghost = wall && y == 0;
                 const T pdm = lowghost ? T(2) * pc[c - 1] - pu[c - 1] : pd[c - 1];
@@ -450,12 +443,10 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
                 const T phi = s.phir(y)[c];
                 const T mu = s.mur(y)[c];
                 const T pv = pc[c];
-                const T ux = s.ux[uo + c], uy = s.uy[uo + c];
-                const T Fx = s.Fx[uo + c], Fy = s.Fy[uo + c];
-                const T lm = s.lmu[uo + c];
+                const T ux = c_ux, uy = c_uy, Fx = c_Fx, Fy = c_Fy, lm = c_lm;
                 const T rho = P.rhoB + (phi - P.phiB) * P.drho;
-                const T gr3x = (c3 * P.drho) * s.gphx[uo + c];   // grad rho / 3
-                const T gr3y = (c3 * P.drho) * s.gphy[uo + c];
+                const T gr3x = (c3 * P.drho) * c_gx;   // grad rho / 3
+                const T gr3y = (c3 * P.drho) * c_gy;
                 T f[9], g[9];
                 SR::read_f(s.fbuf(y), c + HP, f);
                 SR::read_g(s.gbuf(y), c + HP, g);
@@ -522,6 +513,13 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
                 }
             }
         }
+        c_ux = n_ux;
+        c_uy = n_uy;
+        c_Fx = n_Fx;
+        c_Fy = n_Fy;
+        c_lm = n_lm;
+        c_gx = n_gx;
+        c_gy = n_gy;
     }
     cp_async_wait<0>();
 }
