@@ -99,16 +99,29 @@ struct PlainStore {
         for (int i = 1; i < 9; ++i) s += __ldg(b + i * NS);
         return s;
     }
+    // In FP32, g_0 (which stays on its cell) is stored as phi minus the
+    // other eight outgoing values: the collision conserves sum_i g_i = phi
+    // exactly in exact arithmetic, and this keeps it so up to one FP32
+    // rounding per cell, so sum phi does not drift with the rounding of g_0.
+    // FP64 stores the collision's g_0 as computed.
+    __device__ __forceinline__ static C g0_value(const C gv[9], C phi) {
+        if (sizeof(T) != 4) return gv[0];
+        C rest = phi;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) rest -= gv[i];
+        return rest;
+    }
     // fv/gv: final values per source direction i, written to slot sl[i] of
-    // cell kk[i].  phi: the source cell's order parameter (unused here).
+    // cell kk[i].  phi: the source cell's order parameter.
     __device__ __forceinline__ static void store(char *lvl, long long NS, const int sl[9],
                                                  const long long kk[9], const C fv[9],
-                                                 const C gv[9], C /*phi*/) {
+                                                 const C gv[9], C phi) {
         T *b = reinterpret_cast<T *>(lvl);
 #pragma unroll
         for (int i = 0; i < 9; ++i) b[sl[i] * NS + kk[i]] = fv[i];
+        b[9 * NS + kk[0]] = g0_value(gv, phi);  // slot 0 never moves and never bounces
 #pragma unroll
-        for (int i = 0; i < 9; ++i) b[(9 + sl[i]) * NS + kk[i]] = gv[i];
+        for (int i = 1; i < 9; ++i) b[(9 + sl[i]) * NS + kk[i]] = gv[i];
     }
 };
 

@@ -123,12 +123,13 @@ struct StripRow<PlainStore<T>, SW> {
     }
     // Interior push: slot i of cell kb + cy_i nx + cx_i, 32-bit offsets.
     __device__ __forceinline__ static void store_fast(char *lvl, int NS, int nx, int kb,
-                                                      const C fv[9], const C gv[9], C) {
+                                                      const C fv[9], const C gv[9], C phi) {
         T *b = reinterpret_cast<T *>(lvl) + kb;
 #pragma unroll
         for (int i = 0; i < 9; ++i) b[i * NS + D2Q9::cy(i) * nx + D2Q9::cx(i)] = fv[i];
+        b[9 * NS] = PlainStore<T>::g0_value(gv, phi);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) b[(9 + i) * NS + D2Q9::cy(i) * nx + D2Q9::cx(i)] = gv[i];
+        for (int i = 1; i < 9; ++i) b[(9 + i) * NS + D2Q9::cy(i) * nx + D2Q9::cx(i)] = gv[i];
     }
 };
 
