@@ -51,10 +51,15 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+# Sources that define the step kernels (k_strip, k_step) and their launch.
+STEP_SOURCES = ("lbm_internal.h", "lbm_kernels.cuh", "lbm_strip.cuh", "lbm_ops.cuh",
+                "lbm_f64.cu", "lbm_f32.cu", "lbm_f16.cu")
+
+
 def _kernel_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1507_03521_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in STEP_SOURCES:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -124,6 +129,17 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The job's time is the slowest rank's: all-reduce MAX (a no-op
+    without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def time_steps(sim, steps, warmup):
@@ -213,10 +229,7 @@ def measure_batch(lbm, W, args, peak, dist):
     e1.record(st)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     cells = b.cells
     world = dist.get_world_size() if dist is not None else 1
     gbs = BYTES_PER_CELL["f32"] * cells / (ms / args.steps * 1e-3) / 1e9
@@ -317,9 +330,7 @@ def main():
             total, per = time_steps(sim, steps, warmup)
             ckinfo = None
         if dist is not None:
-            t = torch.tensor([total], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
+            total = max_over_ranks(total, dist, "cuda")
             torch.cuda.synchronize()
             dist.barrier()
         return sim, total, per, ckinfo
@@ -407,10 +418,7 @@ def main():
     sim.mass()
     t_e2e = time.perf_counter() - t0
     sim.close()
-    if dist is not None:
-        t = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks(t_e2e, dist, "cuda")
     h2d = phi_h.nbytes
     d2h = sum(v.nbytes for v in outs.values()) + 16
     line["e2e"] = {"value": round(cells * args.steps * world / t_e2e / 1e6, 2), "unit": "MLUPS",
