@@ -79,13 +79,17 @@ struct StripRow<PlainStore<T>, SW> {
         int goff[NCH], soff[NCH];
         int gslot;  // element offset of the g slots: 9 NS
     };
+    // Only the chunks covering the strip's active columns and their halo
+    // (x_start .. x_start + need - 1) are copied: a domain narrower than the
+    // strip would otherwise load the same row several times over.
     __device__ __forceinline__ static void describe(Desc &d, int t, long long NS, int x_start,
-                                                    int nx) {
+                                                    int nx, int need) {
         d.gslot = 9 * (int)NS;
 #pragma unroll
         for (int k = 0; k < NCH; ++k) {
             const int j = t + k * SW;
-            if (j < TOTAL) {
+            const int c0 = (j % CPS) * CE;
+            if (j < TOTAL && c0 < need) {
                 const int sl = j / CPS, c = j - sl * CPS;
                 d.goff[k] = sl * (int)NS + wrap_any(x_start + c * CE, nx);
                 d.soff[k] = sl * LW + c * CE;
@@ -155,12 +159,12 @@ struct StripRow<Store16<H>, SW> {
         unsigned gflt;              // bit k: chunk k of the g row is a g_0 (float) chunk
     };
     __device__ __forceinline__ static void describe(Desc &d, int t, long long NS, int x_start,
-                                                    int nx) {
+                                                    int nx, int need) {
         const int ns = (int)NS;
 #pragma unroll
         for (int k = 0; k < NF; ++k) {
             const int j = t + k * SW;
-            if (j < TF) {
+            if (j < TF && (j % CH) * 8 < need) {
                 const int sl = j / CH, c = j - sl * CH;
                 d.foff[k] = (2 + sl) * ns + wrap_any(x_start + c * 8, nx);
                 d.fso[k] = sl * LW + c * 8;
@@ -173,11 +177,11 @@ struct StripRow<Store16<H>, SW> {
 #pragma unroll
         for (int k = 0; k < NG; ++k) {
             const int j = t + k * SW;
-            if (j < C0) {
+            if (j < C0 && j * 4 < need) {
                 d.goff[k] = wrap_any(x_start + j * 4, nx);
                 d.gso[k] = j * 16;  // bytes
                 d.gflt |= 1u << k;
-            } else if (j < TG) {
+            } else if (j >= C0 && j < TG && ((j - C0) % CH) * 8 < need) {
                 const int jj = j - C0;
                 const int sl = jj / CH, c = jj - sl * CH;
                 d.goff[k] = (2 + 9 + sl) * ns + wrap_any(x_start + c * 8, nx);
@@ -301,7 +305,8 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     const int yfirst = ys - 6;
 
     typename SR::Desc desc;
-    SR::describe(desc, t, P.NS, x0 - HP, nx);
+    const int active = nx - x0 < SW ? nx - x0 : SW;
+    SR::describe(desc, t, P.NS, x0 - HP, nx, active + 2 * HP);
     __syncthreads();
 
     // Iteration y reads g row y+3 and f row y+1 first; both are issued
