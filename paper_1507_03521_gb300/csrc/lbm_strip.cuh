@@ -245,6 +245,7 @@ struct StripRow<Store16<H>, SW> {
 template <class T, class ST, int SW, int DEPTH>
 struct StripSmem {
     using SR = StripRow<ST, SW>;
+    using Tp = T;
     static constexpr int HP = SR::HP;
     static constexpr int LW = SR::LW;
     // g rows are read 3 iterations after they arrive (phi, then collision),
@@ -259,23 +260,48 @@ struct StripSmem {
     static constexpr size_t fld_elems =
         (size_t)RPHI * WPHI + (size_t)RMU * WMU + (size_t)RP * WQ;
     static constexpr size_t bytes = pop_bytes + fld_elems * sizeof(T);
+    // Order in shared memory: NBG g rows, NBF f rows, then the phi, mu and
+    // p rings (RingSlots holds the offsets).
+};
 
-    char *pop;
-    T *phi, *mu, *p;
-    __device__ __forceinline__ StripSmem(char *base) {
-        pop = base;
-        phi = reinterpret_cast<T *>(base + pop_bytes);
-        mu = phi + RPHI * WPHI;
-        p = mu + RMU * WMU;
+// The ring slots of the rows live at iteration y, as byte offsets into the
+// CTA's shared memory (column 0 of the strip for the field rings):
+// g[k], f[k], ph[k], mu[k] hold row y+k and p[k] row y-1+k.  Advancing y
+// rotates the slots (register moves) instead of reducing row indices
+// modulo the ring sizes at every access.
+template <class SM>
+struct RingSlots {
+    using T = typename SM::Tp;
+    int g[SM::NBG], f[SM::NBF], ph[SM::RPHI], mu[SM::RMU], p[SM::RP];
+    __device__ __forceinline__ RingSlots() {
+        constexpr int E = sizeof(T);
+        constexpr int b_mu = (int)SM::pop_bytes + SM::RPHI * SM::WPHI * E;
+        constexpr int b_p = b_mu + SM::RMU * SM::WMU * E;
+#pragma unroll
+        for (int k = 0; k < SM::NBG; ++k) g[k] = k * (int)SM::gb;
+#pragma unroll
+        for (int k = 0; k < SM::NBF; ++k) f[k] = (int)(SM::gb * SM::NBG) + k * (int)SM::fb;
+#pragma unroll
+        for (int k = 0; k < SM::RPHI; ++k) ph[k] = (int)SM::pop_bytes + (k * SM::WPHI + 3) * E;
+#pragma unroll
+        for (int k = 0; k < SM::RMU; ++k) mu[k] = b_mu + (k * SM::WMU + 2) * E;
+#pragma unroll
+        for (int k = 0; k < SM::RP; ++k) p[k] = b_p + (k * SM::WQ + 1) * E;
     }
-    __device__ __forceinline__ char *gbuf(int row) const { return pop + (size_t)((row + 64) % NBG) * gb; }
-    __device__ __forceinline__ char *fbuf(int row) const {
-        return pop + gb * NBG + (size_t)((row + 64) % NBF) * fb;
+    template <int N>
+    __device__ __forceinline__ static void rot(int (&a)[N]) {
+        const int t = a[0];
+#pragma unroll
+        for (int k = 0; k + 1 < N; ++k) a[k] = a[k + 1];
+        a[N - 1] = t;
     }
-    // ring row pointers; column index relative to the strip's first column
-    __device__ __forceinline__ T *phir(int row) const { return phi + ((row + 64) % RPHI) * WPHI + 3; }
-    __device__ __forceinline__ T *mur(int row) const { return mu + ((row + 64) % RMU) * WMU + 2; }
-    __device__ __forceinline__ T *pr(int row) const { return p + ((row + 64) % RP) * WQ + 1; }
+    __device__ __forceinline__ void advance() {
+        rot(g);
+        rot(f);
+        rot(ph);
+        rot(mu);
+        rot(p);
+    }
 };
 
 // Column loop of one step: columns -h .. SW+h-1.  Every thread takes column
@@ -298,7 +324,6 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     using SM = StripSmem<T, ST, SW, DEPTH>;
     using SR = typename SM::SR;
     constexpr int HP = SM::HP;
-    const SM s(smem_raw);
     const int t = threadIdx.x;
     const int nx = P.nx, ny = P.ny, wall = P.wall;
     const int NS = (int)P.NS;
@@ -309,16 +334,20 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     SR::describe(desc, t, P.NS, x0 - HP, nx, active + 2 * HP);
     __syncthreads();
 
+    RingSlots<SM> R;
+    auto at = [&](int off) { return smem_raw + off; };
+    auto atT = [&](int off) { return reinterpret_cast<T *>(smem_raw + off); };
+
     // Iteration y reads g row y+3 and f row y+1 first; both are issued
     // DEPTH iterations earlier, as one commit group.
-    auto issue_for = [&](int it) {
+    auto issue_for = [&](int it, int gslot, int fslot) {
         const int gr = it + 3, fr = it + 1;
-        if (gr <= ye + 2) SR::issue_g(desc, s.gbuf(gr), src, src_row(gr, ny, wall) * nx);
-        if (fr <= ye) SR::issue_f(desc, s.fbuf(fr), src, src_row(fr, ny, wall) * nx);
+        if (gr <= ye + 2) SR::issue_g(desc, at(gslot), src, src_row(gr, ny, wall) * nx);
+        if (fr <= ye) SR::issue_f(desc, at(fslot), src, src_row(fr, ny, wall) * nx);
         cp_async_commit();  // one group per iteration, possibly empty
     };
 #pragma unroll
-    for (int d = 0; d < DEPTH; ++d) issue_for(yfirst + d);
+    for (int d = 0; d < DEPTH; ++d) issue_for(yfirst + d, R.g[d + 3], R.f[d + 1]);
 
     // Interior strips never wrap in x when pushing; interior rows never wrap
     // or bounce in y.
@@ -332,12 +361,12 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     for (int y = yfirst; y < ye; ++y) {
         cp_async_wait<DEPTH - 1>();   // g row y+3, f row y+1 have landed (own chunks)
         __syncthreads();              // ... everyone's; rows y-1 are free
-        issue_for(y + DEPTH);         // into the buffers of g row y-1, f row y-1
+        issue_for(y + DEPTH, R.g[SM::NBG - 1], R.f[SM::NBF - 1]);  // the slots of rows y-1
 
         // 1. phi at row y+3, columns -3 .. SW+2
         {
-            const char *b = s.gbuf(y + 3);
-            T *ph = s.phir(y + 3);
+            const char *b = at(R.g[3]);
+            T *ph = atT(R.ph[3]);
             columns<SW, 3, 3>(t, [&](int c) {
                 T g[9];
                 SR::read_g(b, c + HP, g);
@@ -349,11 +378,11 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
         // 3. mu at row y+2, columns -2 .. SW+1 (Eq. 5)
         {
             const int r = y + 2;
-            T *mo = s.mur(r);
+            T *mo = atT(R.mu[2]);
             const bool ghost = wall && (r < 0 || r >= ny);
             if (!ghost) {
-                const T *pu = s.phir(r + 1), *pc = s.phir(r), *pd = s.phir(r - 1);
-                T *mlow = (wall && r == 0) ? s.mur(-1) : nullptr;
+                const T *pu = atT(R.ph[3]), *pc = atT(R.ph[2]), *pd = atT(R.ph[1]);
+                T *mlow = (wall && r == 0) ? atT(R.mu[1]) : nullptr;  // row -1
                 columns<SW, 2, 1>(t, [&](int c) {
                     const T C = pc[c];
                     // lap = (2/cs2) sum w_i (phi(x + c_i) - phi(x)), differences first
@@ -364,12 +393,12 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
                     mo[c] = m;
                     if (mlow) mlow[c] = m;  // ghost row -1 mirrors row 0
                 });
-            } else if (r >= ny) {
-                const T *mm = s.mur(2 * ny - 1 - r);  // mirror row (already computed)
+            } else if (r == ny) {
+                const T *mm = atT(R.mu[1]);  // mirror row ny-1 (already computed)
                 columns<SW, 2, 1>(t, [&](int c) { mo[c] = mm[c]; });
             }
             // r < 0 at a wall: row -1 is written when row 0 is computed;
-            // rows below are never read.
+            // rows below -1 and above ny are never read.
         }
         __syncthreads();
 
@@ -379,11 +408,11 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
         //    iteration's collision (Eq. 31), in registers.
         {
             const int r = y + 1;
-            T *po = s.pr(r);
+            T *po = atT(R.p[2]);
             if (!wall || (r >= 0 && r < ny)) {
-                const T *pu = s.phir(r + 1), *pc = s.phir(r), *pd = s.phir(r - 1);
-                const T *mu_ = s.mur(r + 1), *mc = s.mur(r), *md = s.mur(r - 1);
-                const char *fbr = s.fbuf(r);
+                const T *pu = atT(R.ph[2]), *pc = atT(R.ph[1]), *pd = atT(R.ph[0]);
+                const T *mu_ = atT(R.mu[2]), *mc = atT(R.mu[1]), *md = atT(R.mu[0]);
+                const char *fbr = at(R.f[1]);
                 auto point = [&](int c, bool keep) {
                     T f[9];
                     SR::read_f(fbr, c + HP, f);
@@ -426,7 +455,7 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
                 if (t >= SW - 32 && t < SW - 30) point(t == SW - 32 ? -1 : SW, false);
             } else if (r == ny) {
                 // ghost row above the top wall: linear extrapolation of p
-                const T *p1 = s.pr(ny - 1), *p2 = s.pr(ny - 2);
+                const T *p1 = atT(R.p[1]), *p2 = atT(R.p[0]);  // rows ny-1, ny-2
                 columns<SW, 1, 0>(t, [&](int c) { po[c] = T(2) * p1[c] - p2[c]; });
             }
         }
@@ -437,7 +466,7 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
             const int c = t;
             const int gx = x0 + c;
             if (gx < nx) {
-                const T *pc = s.pr(y), *pu = s.pr(y + 1), *pd = s.pr(y - 1);
+                const T *pc = atT(R.p[1]), *pu = atT(R.p[2]), *pd = atT(R.p[0]);
                 const bool lowghost = wall && y == 0;
                 const T pdm = lowghost ? T(2) * pc[c - 1] - pu[c - 1] : pd[c - 1];
                 const T pd0 = lowghost ? T(2) * pc[c] - pu[c] : pd[c];
@@ -446,16 +475,16 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
                               T(1.0 / 12.0) * ((pu[c + 1] - pu[c - 1]) + (pdp - pdm));
                 const T gpy = T(1.0 / 3.0) * (pu[c] - pd0) +
                               T(1.0 / 12.0) * ((pu[c + 1] + pu[c - 1]) - (pdm + pdp));
-                const T phi = s.phir(y)[c];
-                const T mu = s.mur(y)[c];
+                const T phi = atT(R.ph[0])[c];
+                const T mu = atT(R.mu[0])[c];
                 const T pv = pc[c];
                 const T ux = c_ux, uy = c_uy, Fx = c_Fx, Fy = c_Fy, lm = c_lm;
                 const T rho = P.rhoB + (phi - P.phiB) * P.drho;
                 const T gr3x = (c3 * P.drho) * c_gx;   // grad rho / 3
                 const T gr3y = (c3 * P.drho) * c_gy;
                 T f[9], g[9];
-                SR::read_f(s.fbuf(y), c + HP, f);
-                SR::read_g(s.gbuf(y), c + HP, g);
+                SR::read_f(at(R.f[0]), c + HP, f);
+                SR::read_g(at(R.g[0]), c + HP, g);
 
                 // per-cell terms (see the collision below)
                 const T uu15 = T(1.5) * (ux * ux + uy * uy);
@@ -526,6 +555,7 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
         c_lm = n_lm;
         c_gx = n_gx;
         c_gy = n_gy;
+        R.advance();
     }
     cp_async_wait<0>();
 }
