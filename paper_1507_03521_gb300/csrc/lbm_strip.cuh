@@ -314,6 +314,134 @@ __device__ __forceinline__ void columns(int t, F &&fn) {
     if ((t >> 5) == (XW % NW) && (t & 31) < 2 * H) fn(SW - H + (t & 31));
 }
 
+// What the collision of one cell needs (Eqs. 22-29): phi, mu, p, rho,
+// u (Eq. 31), F (Eq. 30 with the body force), lap mu, grad phi and grad p.
+template <class T>
+struct CellState {
+    T phi, mu, p, rho, ux, uy, Fx, Fy, lm, gphx, gphy, gpx, gpy;
+};
+
+// BGK collision of one cell with Gamma_i = 1 + s_i: post-collision f*_i
+// (Eqs. 22, 24, 28) and g*_i (Eqs. 23, 25, 27, 29), direction by direction.
+// With Z = F + grad(rho)/3 and D = grad p - F,
+//   F_i-term:  (c_i - u).F + s_i (c_i - u).Z
+//   G_i-term:  (1 + s_i) (c_i - u).D
+template <class T>
+__device__ __forceinline__ void collide(const KP<T> &P, const CellState<T> &c, const T f[9],
+                                        const T g[9], T fv[9], T gv[9]) {
+    const T c3 = T(1.0 / 3.0);
+    const T ux = c.ux, uy = c.uy, Fx = c.Fx, Fy = c.Fy;
+    const T gr3x = (c3 * P.drho) * c.gphx;  // grad rho / 3
+    const T gr3y = (c3 * P.drho) * c.gphy;
+    const T Zx = Fx + gr3x, Zy = Fy + gr3y;
+    const T dx = c.gpx - Fx, dy = c.gpy - Fy;
+    const T uu15 = T(1.5) * (ux * ux + uy * uy);
+    const T uF = ux * Fx + uy * Fy;
+    const T uZ = ux * Zx + uy * Zy;
+    const T uD = ux * dx + uy * dy;
+    const T Q = P.pg * (T(-3) * c.phi * rcp_fast(c.rho));  // pg * (-phi / (cs2 rho))
+    const T Bf = P.itf * (c3 * c.rho);                       // itf cs2 rho
+    const T Kf = P.itf * c.p - P.pf * (c3 * c.rho * P.gl * c.lm);
+    const T omf = T(1) - P.itf, omg = T(1) - P.itg;
+    const T phg = P.itg * c.phi;
+    const T Ag = P.itg * P.alpha * c.mu;                     // itg alpha mu
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int cx = D2Q9::cx(i), cy = D2Q9::cy(i);
+        const T w = T(D2Q9::w(i));
+        const T cu = T(cx) * ux + T(cy) * uy;
+        const T si = cu * (T(3) + T(4.5) * cu) - uu15;  // s_i (Eq. 26)
+        const T eF = (T(cx) * Fx + T(cy) * Fy) - uF;    // (c_i - u).F
+        const T eZ = (T(cx) * Zx + T(cy) * Zy) - uZ;    // (c_i - u).Z
+        const T eD = (T(cx) * dx + T(cy) * dy) - uD;    // (c_i - u).D
+        fv[i] = omf * f[i] + w * (Kf + Bf * si + P.pf * (eF + si * eZ));
+        const T Hg = (i == 0) ? (phg - T(1.0 - D2Q9::w(0)) * Ag) * T(1.0 / D2Q9::w(0)) : Ag;
+        gv[i] = omg * g[i] + w * (Hg + phg * si + Q * (eD + si * eD));
+    }
+}
+
+// FP32: the same arithmetic with directions (1,2), (3,4), (5,6), (7,8) in
+// the two lanes of packed f32x2 operations.  Direction 3 is -1 times
+// direction 1 (4 of 2, 7 of 5, 8 of 6), so both pairs of a class share the
+// products c_i.u, c_i.F, c_i.Z, c_i.D and differ in sign only.
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
+template <int SGN>
+__device__ __forceinline__ void collide_pair(float2 cu, float2 cF, float2 cZ, float2 cD, float w,
+                                             float2 mu15, float2 muF, float2 muZ, float2 muD,
+                                             float2 Kf, float2 Bf, float2 pf, float2 omf,
+                                             float2 Ag, float2 phg, float2 Q, float2 omg,
+                                             float2 f, float2 g, float2 &fo, float2 &go) {
+    const float2 sg = bc2(float(SGN));
+    // s_i = (SGN cu)(3 + 4.5 SGN cu) - 1.5 u.u = cu (4.5 cu + 3 SGN) - 1.5 u.u
+    const float2 si = __ffma2_rn(cu, __ffma2_rn(cu, bc2(4.5f), bc2(3.0f * SGN)), mu15);
+    const float2 eF = __ffma2_rn(cF, sg, muF);
+    const float2 eZ = __ffma2_rn(cZ, sg, muZ);
+    const float2 eD = __ffma2_rn(cD, sg, muD);
+    const float2 w2 = bc2(w);
+    float2 a = __ffma2_rn(Bf, si, Kf);
+    a = __ffma2_rn(pf, __ffma2_rn(si, eZ, eF), a);
+    fo = __ffma2_rn(omf, f, __fmul2_rn(w2, a));
+    float2 b = __ffma2_rn(phg, si, Ag);
+    b = __ffma2_rn(Q, __ffma2_rn(si, eD, eD), b);
+    go = __ffma2_rn(omg, g, __fmul2_rn(w2, b));
+}
+
+__device__ __forceinline__ void collide(const KP<float> &P, const CellState<float> &c,
+                                        const float f[9], const float g[9], float fv[9],
+                                        float gv[9]) {
+    const float c3 = 1.0f / 3.0f;
+    const float ux = c.ux, uy = c.uy, Fx = c.Fx, Fy = c.Fy;
+    const float Zx = Fx + (c3 * P.drho) * c.gphx, Zy = Fy + (c3 * P.drho) * c.gphy;
+    const float dx = c.gpx - Fx, dy = c.gpy - Fy;
+    const float uu15 = 1.5f * (ux * ux + uy * uy);
+    const float uF = ux * Fx + uy * Fy;
+    const float uZ = ux * Zx + uy * Zy;
+    const float uD = ux * dx + uy * dy;
+    const float Q = P.pg * (-3.0f * c.phi * rcp_fast(c.rho));
+    const float Bf = P.itf * (c3 * c.rho);
+    const float Kf = P.itf * c.p - P.pf * (c3 * c.rho * P.gl * c.lm);
+    const float omf = 1.0f - P.itf, omg = 1.0f - P.itg;
+    const float phg = P.itg * c.phi;
+    const float Ag = P.itg * P.alpha * c.mu;
+    // direction 0 (c_0 = 0)
+    {
+        const float w = float(D2Q9::w(0));
+        const float si = -uu15;
+        fv[0] = omf * f[0] + w * (Kf + Bf * si + P.pf * (-uF - si * uZ));
+        const float H0 = (phg - float(1.0 - D2Q9::w(0)) * Ag) * float(1.0 / D2Q9::w(0));
+        gv[0] = omg * g[0] + w * (H0 + phg * si + Q * (-uD - si * uD));
+    }
+    const float2 mu15 = bc2(-uu15), muF = bc2(-uF), muZ = bc2(-uZ), muD = bc2(-uD);
+    const float2 Kf2 = bc2(Kf), Bf2 = bc2(Bf), pf2 = bc2(P.pf), omf2 = bc2(omf);
+    const float2 Ag2 = bc2(Ag), phg2 = bc2(phg), Q2 = bc2(Q), omg2 = bc2(omg);
+    float2 fo, go;
+    // axis directions: (1,2) = +(e_x, e_y), (3,4) = -(e_x, e_y)
+    {
+        const float2 cu = make_float2(ux, uy), cF = make_float2(Fx, Fy);
+        const float2 cZ = make_float2(Zx, Zy), cD = make_float2(dx, dy);
+        const float w = float(D2Q9::w(1));
+        collide_pair<1>(cu, cF, cZ, cD, w, mu15, muF, muZ, muD, Kf2, Bf2, pf2, omf2, Ag2, phg2, Q2,
+                        omg2, make_float2(f[1], f[2]), make_float2(g[1], g[2]), fo, go);
+        fv[1] = fo.x, fv[2] = fo.y, gv[1] = go.x, gv[2] = go.y;
+        collide_pair<-1>(cu, cF, cZ, cD, w, mu15, muF, muZ, muD, Kf2, Bf2, pf2, omf2, Ag2, phg2, Q2,
+                         omg2, make_float2(f[3], f[4]), make_float2(g[3], g[4]), fo, go);
+        fv[3] = fo.x, fv[4] = fo.y, gv[3] = go.x, gv[4] = go.y;
+    }
+    // diagonals: (5,6) = +((1,1), (-1,1)), (7,8) = -((1,1), (-1,1))
+    {
+        const float2 cu = make_float2(ux + uy, uy - ux), cF = make_float2(Fx + Fy, Fy - Fx);
+        const float2 cZ = make_float2(Zx + Zy, Zy - Zx), cD = make_float2(dx + dy, dy - dx);
+        const float w = float(D2Q9::w(5));
+        collide_pair<1>(cu, cF, cZ, cD, w, mu15, muF, muZ, muD, Kf2, Bf2, pf2, omf2, Ag2, phg2, Q2,
+                        omg2, make_float2(f[5], f[6]), make_float2(g[5], g[6]), fo, go);
+        fv[5] = fo.x, fv[6] = fo.y, gv[5] = go.x, gv[6] = go.y;
+        collide_pair<-1>(cu, cF, cZ, cD, w, mu15, muF, muZ, muD, Kf2, Bf2, pf2, omf2, Ag2, phg2, Q2,
+                         omg2, make_float2(f[7], f[8]), make_float2(g[7], g[8]), fo, go);
+        fv[7] = fo.x, fv[8] = fo.y, gv[7] = go.x, gv[8] = go.y;
+    }
+}
+
 // One work item of the strip form: columns x0 .. x0+SW-1 (clipped to nx),
 // rows ys .. ye-1 of one domain, read from level `src`, written to `dst`.
 // The leading barrier also separates consecutive items of one CTA.
@@ -352,7 +480,7 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     // Interior strips never wrap in x when pushing; interior rows never wrap
     // or bounce in y.
     const bool x_inner = x0 > 0 && x0 + SW < nx;
-    const T c3 = T(1.0 / 3.0), c6 = T(0.5 / 3.0);
+    const T c6 = T(0.5 / 3.0);
     // u, F, lap mu, grad phi of column t: c_* at row y (from the previous
     // iteration), n_* at row y+1 (computed in step 4 of this iteration)
     T c_ux = 0, c_uy = 0, c_Fx = 0, c_Fy = 0, c_lm = 0, c_gx = 0, c_gy = 0;
@@ -478,46 +606,14 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
                 const T phi = atT(R.ph[0])[c];
                 const T mu = atT(R.mu[0])[c];
                 const T pv = pc[c];
-                const T ux = c_ux, uy = c_uy, Fx = c_Fx, Fy = c_Fy, lm = c_lm;
                 const T rho = P.rhoB + (phi - P.phiB) * P.drho;
-                const T gr3x = (c3 * P.drho) * c_gx;   // grad rho / 3
-                const T gr3y = (c3 * P.drho) * c_gy;
                 T f[9], g[9];
                 SR::read_f(at(R.f[0]), c + HP, f);
                 SR::read_g(at(R.g[0]), c + HP, g);
-
-                // per-cell terms (see the collision below)
-                const T uu15 = T(1.5) * (ux * ux + uy * uy);
-                const T irho = rcp_fast(rho);
-                const T Q = P.pg * (T(-3) * phi * irho);           // pg * (-phi / (cs2 rho))
-                const T dx = gpx - Fx, dy = gpy - Fy;
-                const T uF = ux * Fx + uy * Fy;
-                const T uR3 = ux * gr3x + uy * gr3y;
-                const T uD = ux * dx + uy * dy;
-                const T Bf = P.itf * (c3 * rho);                    // itf cs2 rho
-                const T Kf = P.itf * pv - P.pf * (c3 * rho * P.gl * lm);
-                const T omf = T(1) - P.itf, omg = T(1) - P.itg;
-                const T phg = P.itg * phi;
-                const T Ag = P.itg * P.alpha * mu;                  // itg alpha mu
                 T fv[9], gv[9];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const int cx = D2Q9::cx(i), cy = D2Q9::cy(i);
-                    const T w = T(D2Q9::w(i));
-                    const T cu = T(cx) * ux + T(cy) * uy;
-                    const T si = cu * (T(3) + T(4.5) * cu) - uu15;   // s_i (Eq. 26)
-                    const T eF = (T(cx) * Fx + T(cy) * Fy) - uF;       // (c_i - u).F
-                    const T eR = (T(cx) * gr3x + T(cy) * gr3y) - uR3;  // (c_i - u).grad rho / 3
-                    const T eD = (T(cx) * dx + T(cy) * dy) - uD;       // (c_i - u).(grad p - F)
-                    // f* = f - (f - f^eq)/tau_f + (1 - 1/2tau_f) F_i  (Eqs. 22, 24, 28)
-                    const T t1 = eF + si * (eF + eR);
-                    fv[i] = omf * f[i] + w * (Kf + Bf * si + P.pf * t1);
-                    // g* = g - (g - g^eq)/tau_g + (1 - 1/2tau_g) G_i  (Eqs. 23, 25, 27, 29)
-                    const T t2 = eD + si * eD;
-                    const T Hg = (i == 0) ? (phg - T(1.0 - D2Q9::w(0)) * Ag) * T(1.0 / D2Q9::w(0))
-                                          : Ag;
-                    gv[i] = omg * g[i] + w * (Hg + phg * si + Q * t2);
-                }
+                collide(P, CellState<T>{phi, mu, pv, rho, c_ux, c_uy, c_Fx, c_Fy, c_lm, c_gx, c_gy,
+                                        gpx, gpy},
+                        f, g, fv, gv);
                 const bool y_inner = y > 0 && y < ny - 1;
                 if (x_inner && y_inner) {
                     SR::store_fast(dst, NS, nx, y * nx + gx, fv, gv, phi);
