@@ -241,6 +241,41 @@ def measure_batch(lbm, W, args, peak, dist):
             "launches_per_step": 1, "kernel": "k_strip_batch<float>"}
 
 
+def measure_slabs(lbm, p, phi, args, mlups_single, dist, n_slabs=4):
+    """The same FP32 workload as the headline, decomposed into n_slabs
+    y-slabs stepped separately with device-to-device ghost exchange (the
+    domain decomposition of the step, run on this one GPU): the cost of
+    the exchange against the whole-domain step."""
+    import torch
+    sim = lbm.Sim(p, "f32")
+    sim.init_phi(phi)
+    s0, _ = sim.get_state()
+    sim.close()
+    sl = lbm.Slabs(p, "f32", n_slabs=n_slabs)
+    sl.scatter(s0, 0)
+    sl.step(args.warmup)
+    st = sl.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0.record(st)
+    sl.step(args.steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    world = dist.get_world_size() if dist is not None else 1
+    cells = p["nx"] * p["ny"]
+    mlups = cells * args.steps * world / (ms * 1e-3) / 1e6
+    # bytes the exchange moves per step (read once, written once): per slab
+    # edge 12 crossing slot-rows and 2 x 18 slots x 3 halo rows, 4 B a value
+    exch = n_slabs * (12 + 2 * 18 * 3) * p["nx"] * 4 * 2
+    sl.close()
+    return {"n_slabs": n_slabs, "mlups": round(mlups, 2), "ms_per_step": round(ms / args.steps, 5),
+            "vs_whole_domain": round(mlups / mlups_single, 4),
+            "launches_per_step": n_slabs + 2, "exchange_bytes_per_step": exch}
+
+
 def measure_adjoint(W):
     """Adjoint workload: droplet in shear, 512 x 512, R = 64, walls at
     +-0.01, rho ratio 10, FP32, 4000 steps, checkpoints every 200 steps;
@@ -288,6 +323,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the f16s/bf16s/f64 forms")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
+    ap.add_argument("--no-slabs", action="store_true", help="skip the y-slab decomposition")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -395,6 +431,8 @@ def main():
 
     if not args.no_batch:
         line["batched"] = measure_batch(lbm, W, args, peak, dist)
+    if not args.no_slabs:
+        line["slabs"] = measure_slabs(lbm, p, phi, args, mlups, dist)
     if not args.no_adjoint:
         line["adjoint"] = measure_adjoint(W)
 

@@ -250,6 +250,52 @@ LBM_API int lbm_batch_segment(const lbm_batch *b);
 LBM_API const char *lbm_batch_last_error(const lbm_batch *b);
 LBM_API void lbm_batch_destroy(lbm_batch *b);
 
+/* ------------------------------------------------------------------ y-slabs
+ * One domain decomposed into n y-slabs that are stepped separately and
+ * exchange ghost rows: the domain decomposition of the step (Eqs. 22-32 act
+ * within 3 rows: grad p <- p <- lap mu <- lap phi), with every slab on the
+ * handle's device and device-to-device copies.  Slab i owns global rows
+ * a_i .. b_i - 1 and holds 3 ghost rows on each side (across the wrap when
+ * periodic in y; ghost rows past a wall are not used).  A step is
+ *   1. the strip kernel on each slab's own rows,
+ *   2. one copy launch moving the populations pushed across each slab edge
+ *      (f and g slots 2, 5, 6 upward; 4, 7, 8 downward) to the slab that
+ *      owns their row,
+ *   3. one copy launch refreshing every ghost row (all 18 slots).
+ * Every cell runs the same kernel body as lbm_step, so the gathered state
+ * is bit-identical to stepping the whole domain.  Requirements: nx a
+ * multiple of 8; every slab >= 3 rows.  `row_starts` (n entries, the first
+ * 0, increasing) gives a_i; NULL splits ny evenly.  States are levels in
+ * the layout of lbm_get_state for the whole domain (device memory).
+ */
+typedef struct lbm_slabs lbm_slabs; /* opaque handle, owned by the caller */
+
+/* Device bytes of the slabs' populations (two levels each) and of the work
+ * buffer (the copy tables).  Errors: LBM_ERR_ARG (message in
+ * lbm_create_error). */
+LBM_API lbm_status lbm_slabs_buffer_sizes(const lbm_params *prm, int n_slabs,
+                                          const int *row_starts, size_t *state_bytes,
+                                          size_t *work_bytes);
+/* Validate (as lbm_create plus the slab requirements) and create. */
+LBM_API lbm_status lbm_slabs_create(const lbm_params *prm, int n_slabs, const int *row_starts,
+                                    void *stream, lbm_slabs **out);
+/* Bind caller-owned, 256-byte aligned device buffers and upload the copy
+ * tables (synchronises the stream). */
+LBM_API lbm_status lbm_slabs_bind_buffers(lbm_slabs *s, void *state, size_t state_bytes,
+                                          void *work, size_t work_bytes);
+/* Load a whole-domain level (device) into the slabs, ghost rows included,
+ * and set the step counter. */
+LBM_API lbm_status lbm_slabs_scatter(lbm_slabs *s, const void *level, int64_t step);
+/* Write the slabs' current state as a whole-domain level (device). */
+LBM_API lbm_status lbm_slabs_gather(lbm_slabs *s, void *level, int64_t *step);
+/* Advance n steps (asynchronous on the stream; n + 2 launches per step). */
+LBM_API lbm_status lbm_slabs_step(lbm_slabs *s, int64_t n);
+/* Rows a_i .. b_i - 1 owned by slab i. */
+LBM_API lbm_status lbm_slabs_rows(const lbm_slabs *s, int i, int *a, int *b);
+LBM_API int64_t lbm_slabs_step_count(const lbm_slabs *s);
+LBM_API const char *lbm_slabs_last_error(const lbm_slabs *s);
+LBM_API void lbm_slabs_destroy(lbm_slabs *s);
+
 /* The mass diagnostic of lbm_mass for callers that cannot allocate device
  * memory.  The paper has no counterpart: this is a library convenience.
  *

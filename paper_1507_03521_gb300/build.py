@@ -28,6 +28,7 @@ UNITS = {
     "lbm_f16": [],
     "lbm_noalloc": [],
     "lbm_batch": [],
+    "lbm_slabs": [],
 }
 
 

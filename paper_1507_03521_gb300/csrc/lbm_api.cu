@@ -26,6 +26,27 @@ thread_local std::string g_create_err;
 
 size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 
+struct Layout {
+    size_t level, state, field_slot, part_off, out_off, work;
+};
+
+Layout layout(const Derived &d, const Ops *ops) {
+    Layout L;
+    L.level = round256(ops->level_bytes(d.NS));
+    L.state = 2 * L.level;
+    L.field_slot = round256((size_t)d.NS * ops->field_size);
+    L.part_off = kFieldSlots * L.field_slot;
+    L.out_off = L.part_off + round256((size_t)kPartBlocks * 5 * sizeof(double));
+    L.work = L.out_off + 256;
+    return L;
+}
+
+}  // namespace
+
+void lbm_internal_set_error(const char *msg) { g_create_err = msg ? msg : ""; }
+
+namespace lbm {
+
 const Ops *ops_for(int dtype) {
     switch (dtype) {
         case LBM_F64: return lbm::ops_f64();
@@ -65,6 +86,11 @@ Derived derive(const lbm_params *p) {
     d.wall = p->bc_y == LBM_WALL;
     d.N = (long long)p->nx * p->ny;
     d.NS = (d.N + 127) / 128 * 128;
+    d.slab = 0;
+    d.y0 = 0;
+    d.rows = d.ny;
+    d.ya = 0;
+    d.yb = d.ny;
     const double dphi = p->phi_A - p->phi_B;
     d.phiA = p->phi_A;
     d.phiB = p->phi_B;
@@ -85,24 +111,11 @@ Derived derive(const lbm_params *p) {
     return d;
 }
 
-struct Layout {
-    size_t level, state, field_slot, part_off, out_off, work;
-};
+}  // namespace lbm
 
-Layout layout(const Derived &d, const Ops *ops) {
-    Layout L;
-    L.level = round256(ops->level_bytes(d.NS));
-    L.state = 2 * L.level;
-    L.field_slot = round256((size_t)d.NS * ops->field_size);
-    L.part_off = kFieldSlots * L.field_slot;
-    L.out_off = L.part_off + round256((size_t)kPartBlocks * 5 * sizeof(double));
-    L.work = L.out_off + 256;
-    return L;
-}
-
-}  // namespace
-
-void lbm_internal_set_error(const char *msg) { g_create_err = msg ? msg : ""; }
+using lbm::check_params;
+using lbm::derive;
+using lbm::ops_for;
 
 namespace lbm {
 // Adjoint work buffer: A_COUNT field arrays of NS elements, then the

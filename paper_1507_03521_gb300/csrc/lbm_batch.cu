@@ -20,6 +20,8 @@
 using lbm::BatchItem;
 using lbm::Derived;
 using lbm::Ops;
+using lbm::derive;
+using lbm::ops_for;
 
 namespace {
 
@@ -27,44 +29,6 @@ constexpr int kMinSeg = 16;            // smallest segment height the item table
 constexpr int kPartBlocks = 152 * 4;   // per-domain mass reduction grid
 
 size_t r256(size_t b) { return (b + 255) & ~size_t(255); }
-
-const Ops *ops_for(int dtype) {
-    switch (dtype) {
-        case LBM_F64: return lbm::ops_f64();
-        case LBM_F32: return lbm::ops_f32();
-        case LBM_F16S: return lbm::ops_f16s();
-        case LBM_BF16S: return lbm::ops_bf16s();
-        default: return nullptr;
-    }
-}
-
-// Derived parameters of one domain (same derivation as lbm_create).
-Derived derive(const lbm_params *p) {
-    Derived d;
-    d.nx = p->nx;
-    d.ny = p->ny;
-    d.wall = p->bc_y == LBM_WALL;
-    d.N = (long long)p->nx * p->ny;
-    d.NS = (d.N + 127) / 128 * 128;
-    const double dphi = p->phi_A - p->phi_B;
-    d.phiA = p->phi_A;
-    d.phiB = p->phi_B;
-    d.phibar = 0.5 * (p->phi_A + p->phi_B);
-    d.rhoB = p->rho_B;
-    d.drho = (p->rho_A - p->rho_B) / dphi;
-    d.kappa = 3.0 * p->sigma * p->W / (2.0 * dphi * dphi);
-    d.beta = 12.0 * p->sigma / (p->W * dphi * dphi * dphi * dphi);
-    d.lambda = p->M;
-    d.alpha = p->M / ((p->tau_g - 0.5) / 3.0);
-    d.gamma = (p->rho_A - p->rho_B) / (p->rho_B * p->phi_A - p->rho_A * p->phi_B);
-    d.grav = p->gravity;
-    d.rhoref = p->rho_ref;
-    d.tau_f = p->tau_f;
-    d.tau_g = p->tau_g;
-    d.uwb = d.wall ? p->u_wall_bottom : 0.0;
-    d.uwt = d.wall ? p->u_wall_top : 0.0;
-    return d;
-}
 
 struct Plan {
     std::vector<Derived> d;

@@ -5,12 +5,19 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <string>
+
+#include "lbm.h"
+
 namespace lbm {
 
 // Host-side derived parameters of one domain (FP64).
 struct Derived {
     int nx, ny, wall;
     long long N, NS;  // cell count and padded slot stride
+    // rows held and stepped by the strip kernel (KP in lbm_kernels.cuh):
+    // the whole domain, or one y-slab of a decomposed domain
+    int slab, y0, rows, ya, yb;
     double phiA, phiB, phibar, rhoB, drho;
     double kappa, beta, alpha, lambda, gamma;
     double grav, rhoref, tau_f, tau_g, uwb, uwt;
@@ -42,6 +49,9 @@ struct Ops {
     const char *name;
     size_t field_size;  // bytes of one field element (8 for FP64, else 4)
     size_t (*level_bytes)(long long NS);
+    // byte offset and element size of population slot q (f_0..f_8 = 0..8,
+    // g_0..g_8 = 9..17) within a level
+    void (*slot_span)(long long NS, int q, size_t *off, size_t *elem);
     cudaError_t (*step)(const Derived &, const void *src, void *dst, cudaStream_t s);
     cudaError_t (*fields)(const Derived &, const void *lvl, void *phi, void *rho, void *p,
                           void *ux, void *uy, void *mu, void *P, cudaStream_t s);
@@ -73,6 +83,13 @@ const Ops *ops_f64();
 const Ops *ops_f32();
 const Ops *ops_f16s();
 const Ops *ops_bf16s();
+
+// Launchers for an lbm_dtype value (null if unknown).
+const Ops *ops_for(int dtype);
+// Parameter checks of lbm_create; empty when p is valid.
+std::string check_params(const lbm_params *p);
+// Derived parameters of the whole domain (Eqs. 3-4 solved, 13, 17, 33).
+Derived derive(const lbm_params *p);
 
 }  // namespace lbm
 

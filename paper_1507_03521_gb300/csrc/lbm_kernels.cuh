@@ -60,6 +60,11 @@ template <class T>
 struct KP {
     int nx, ny, wall;
     long long NS;           // slot stride (padded cell count)
+    // Rows held and stepped (strip kernel).  The whole domain: slab = 0,
+    // y0 = 0, rows = ny, ya..yb = 0..ny.  A y-slab of a decomposed domain:
+    // slab = 1, the level holds global rows y0 .. y0+rows-1 (its own rows
+    // ya..yb-1 and 3 ghost rows on each side), with no wrap in y.
+    int slab, y0, rows, ya, yb;
     T phiA, phiB, phibar;   // bulk order parameters and their mean
     T rhoB, drho;           // rho = rhoB + (phi - phiB) drho (Eq. 11)
     T kappa, beta4, beta;   // kappa, 4 beta, beta
@@ -84,6 +89,12 @@ struct PlainStore {
     using C = T;
     static constexpr size_t level_bytes_per_cell = 18 * sizeof(T);
     static size_t level_bytes(long long NS) { return (size_t)NS * 18 * sizeof(T); }
+    // Byte offset and element size of population slot q (f_0..f_8 = 0..8,
+    // g_0..g_8 = 9..17) within a level.
+    static void slot_span(long long NS, int q, size_t *off, size_t *elem) {
+        *off = (size_t)q * NS * sizeof(T);
+        *elem = sizeof(T);
+    }
     __device__ __forceinline__ static void load(const char *lvl, long long NS, long long k,
                                                 C f[9], C g[9]) {
         const T *b = reinterpret_cast<const T *>(lvl);
@@ -162,6 +173,17 @@ struct Store16 {
     using C = float;
     using E = HalfStore<H>;
     static size_t level_bytes(long long NS) { return (size_t)NS * (4 + 17 * 2); }
+    // slot q (f_0..f_8 = 0..8, g_0..g_8 = 9..17): g_0 in FP32 first, then
+    // the 16-bit slots f_0..f_8, g_1..g_8
+    static void slot_span(long long NS, int q, size_t *off, size_t *elem) {
+        if (q == 9) {
+            *off = 0;
+            *elem = 4;
+        } else {
+            *off = (size_t)NS * 4 + (size_t)(q < 9 ? q : q - 1) * NS * 2;
+            *elem = 2;
+        }
+    }
     // slot index of f_i: i; of g_i (i >= 1): 8 + i
     __device__ __forceinline__ static void load(const char *lvl, long long NS, long long k,
                                                 C f[9], C g[9]) {

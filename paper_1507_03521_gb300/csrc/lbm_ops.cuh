@@ -18,6 +18,11 @@ inline KP<T> make_kp(const Derived &d) {
     k.ny = d.ny;
     k.wall = d.wall;
     k.NS = d.NS;
+    k.slab = d.slab;
+    k.y0 = d.y0;
+    k.rows = d.rows;
+    k.ya = d.ya;
+    k.yb = d.yb;
     k.phiA = T(d.phiA);
     k.phiB = T(d.phiB);
     k.phibar = T(d.phibar);
@@ -58,6 +63,7 @@ struct OpsImpl {
 
     // Opt in to the strip kernel's shared memory and size the grid to
     // one wave: strips x segments ~= resident CTAs, segments >= 16 rows.
+    template <bool SLAB>
     static cudaError_t strip_grid(const Derived &d, dim3 &grid, int &seg_h) {
         static StripCfg cfg[64];
         int dev = 0;
@@ -66,11 +72,11 @@ struct OpsImpl {
         if (dev >= 64) return cudaErrorInvalidDevice;
         StripCfg &c = cfg[dev];
         if (!c.ready) {
-            e = cudaFuncSetAttribute(k_strip<T, ST, SW, DEPTH>,
+            e = cudaFuncSetAttribute(k_strip<T, ST, SW, DEPTH, SLAB>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
             if (e != cudaSuccess) return e;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.per_sm, k_strip<T, ST, SW, DEPTH>,
-                                                              SW, SM::bytes);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &c.per_sm, k_strip<T, ST, SW, DEPTH, SLAB>, SW, SM::bytes);
             if (e != cudaSuccess) return e;
             e = cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
             if (e != cudaSuccess) return e;
@@ -78,15 +84,27 @@ struct OpsImpl {
             c.ready = true;
         }
         const int strips = (d.nx + SW - 1) / SW;
+        const int rows = d.yb - d.ya;  // rows stepped
         long long slots = (long long)c.per_sm * c.sms;
         long long nseg = slots / strips;
         if (nseg < 1) nseg = 1;
-        const long long max_seg = (d.ny + 15) / 16;
+        const long long max_seg = (rows + 15) / 16;
         if (nseg > max_seg) nseg = max_seg;
-        seg_h = (int)((d.ny + nseg - 1) / nseg);
-        nseg = (d.ny + seg_h - 1) / seg_h;
+        seg_h = (int)((rows + nseg - 1) / nseg);
+        nseg = (rows + seg_h - 1) / seg_h;
         grid = dim3((unsigned)strips, (unsigned)nseg);
         return cudaSuccess;
+    }
+
+    template <bool SLAB>
+    static cudaError_t strip_step(const Derived &d, const void *src, void *dst, cudaStream_t s) {
+        dim3 grid;
+        int seg_h = 0;
+        cudaError_t e = strip_grid<SLAB>(d, grid, seg_h);
+        if (e != cudaSuccess) return e;
+        k_strip<T, ST, SW, DEPTH, SLAB><<<grid, SW, SM::bytes, s>>>(
+            static_cast<const char *>(src), static_cast<char *>(dst), make_kp<T>(d), seg_h);
+        return cudaGetLastError();
     }
 
     template <int MODE>
@@ -110,15 +128,9 @@ struct OpsImpl {
     }
 
     static cudaError_t step(const Derived &d, const void *src, void *dst, cudaStream_t s) {
-        if (strip_ok(d)) {
-            dim3 grid;
-            int seg_h = 0;
-            cudaError_t e = strip_grid(d, grid, seg_h);
-            if (e != cudaSuccess) return e;
-            k_strip<T, ST, SW, DEPTH><<<grid, SW, SM::bytes, s>>>(
-                static_cast<const char *>(src), static_cast<char *>(dst), make_kp<T>(d), seg_h);
-            return cudaGetLastError();
-        }
+        // a y-slab (lbm_slabs.cu) has been checked for the strip form
+        if (d.slab) return strip_ok(d) ? strip_step<true>(d, src, dst, s) : cudaErrorInvalidValue;
+        if (strip_ok(d)) return strip_step<false>(d, src, dst, s);
         cudaError_t e = prepare<MODE_STEP>();
         if (e != cudaSuccess) return e;
         k_step<T, ST, RPT, MODE_STEP><<<grid(d), dim3(32, 8), TL::bytes, s>>>(
@@ -283,7 +295,8 @@ struct OpsImpl {
     }
 
     static const Ops *ops(const char *name) {
-        static const Ops o = {name,           sizeof(T),      &level_bytes,      &step,
+        static const Ops o = {name,           sizeof(T),      &level_bytes,      &ST::slot_span,
+                              &step,
                               &fields,        &init,          &mass,             &laplace,
                               SW,             &strip_ok,      sizeof(BatchDom<T>), &batch_fill_dom,
                               &batch_slots,   &batch_step,

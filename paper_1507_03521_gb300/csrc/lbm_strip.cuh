@@ -304,6 +304,20 @@ struct RingSlots {
     }
 };
 
+// Row of the level buffer that holds global row y.  The whole domain wraps
+// rows outside 0..ny-1 (periodic) or mirrors them (walls).  A slab holds
+// rows y0 .. y0+rows-1, whose ghost rows its neighbours filled in (or, at a
+// wall, mirrors into its own rows); rows beyond that feed only warm-up
+// results that are never used, so they are clamped to the buffer.
+template <bool SLAB, class T>
+__device__ __forceinline__ int buf_row(const KP<T> &P, int y) {
+    if (!SLAB) return src_row(y, P.ny, P.wall);
+    int m = y;
+    if (P.wall) m = y < 0 ? -y - 1 : (y >= P.ny ? 2 * P.ny - 1 - y : y);
+    const int l = m - P.y0;
+    return l < 0 ? 0 : (l >= P.rows ? P.rows - 1 : l);
+}
+
 // Column loop of one step: columns -h .. SW+h-1.  Every thread takes column
 // t - h; the 2h columns past SW-h are taken by the first 2h lanes of warp
 // `xw` (a different warp per step), so no warp carries every extra pass.
@@ -445,7 +459,7 @@ __device__ __forceinline__ void collide(const KP<float> &P, const CellState<floa
 // One work item of the strip form: columns x0 .. x0+SW-1 (clipped to nx),
 // rows ys .. ye-1 of one domain, read from level `src`, written to `dst`.
 // The leading barrier also separates consecutive items of one CTA.
-template <class T, class ST, int SW, int DEPTH>
+template <class T, class ST, int SW, int DEPTH, bool SLAB = false>
 __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *__restrict__ dst,
                                            const KP<T> &P, const int x0, const int ys,
                                            const int ye, char *smem_raw) {
@@ -470,8 +484,8 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     // DEPTH iterations earlier, as one commit group.
     auto issue_for = [&](int it, int gslot, int fslot) {
         const int gr = it + 3, fr = it + 1;
-        if (gr <= ye + 2) SR::issue_g(desc, at(gslot), src, src_row(gr, ny, wall) * nx);
-        if (fr <= ye) SR::issue_f(desc, at(fslot), src, src_row(fr, ny, wall) * nx);
+        if (gr <= ye + 2) SR::issue_g(desc, at(gslot), src, buf_row<SLAB>(P, gr) * nx);
+        if (fr <= ye) SR::issue_f(desc, at(fslot), src, buf_row<SLAB>(P, fr) * nx);
         cp_async_commit();  // one group per iteration, possibly empty
     };
 #pragma unroll
@@ -614,13 +628,16 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
                 collide(P, CellState<T>{phi, mu, pv, rho, c_ux, c_uy, c_Fx, c_Fy, c_lm, c_gx, c_gy,
                                         gpx, gpy},
                         f, g, fv, gv);
-                const bool y_inner = y > 0 && y < ny - 1;
+                // pushes that neither wrap nor meet a wall (a slab's pushes
+                // across its edges land in its ghost rows)
+                const bool y_inner = (y > 0 && y < ny - 1) || (SLAB && !wall);
+                const int yl = SLAB ? y - P.y0 : y;  // row within the level
                 if (x_inner && y_inner) {
-                    SR::store_fast(dst, NS, nx, y * nx + gx, fv, gv, phi);
+                    SR::store_fast(dst, NS, nx, yl * nx + gx, fv, gv, phi);
                 } else {
                     int sl[9];
                     long long kk[9];
-                    const long long k = (long long)y * nx + gx;
+                    const long long k = (long long)yl * nx + gx;
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
                         const int cx = D2Q9::cx(i), cy = D2Q9::cy(i);
@@ -635,7 +652,8 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
                         } else {
                             int xd = gx + cx;
                             xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
-                            const int yy = yd < 0 ? yd + ny : (yd >= ny ? yd - ny : yd);
+                            const int yy = SLAB ? yd - P.y0
+                                                : (yd < 0 ? yd + ny : (yd >= ny ? yd - ny : yd));
                             sl[i] = i;
                             kk[i] = (long long)yy * nx + xd;
                         }
@@ -656,15 +674,16 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     cp_async_wait<0>();
 }
 
-// Single domain: CTA (bx, by) owns strip bx and segment by.
-template <class T, class ST, int SW, int DEPTH>
+// Single domain (or one y-slab of it, SLAB): CTA (bx, by) owns strip bx
+// and segment by of rows ya .. yb-1.
+template <class T, class ST, int SW, int DEPTH, bool SLAB>
 __global__ void __launch_bounds__(SW)
 k_strip(const char *__restrict__ src, char *__restrict__ dst, const __grid_constant__ KP<T> P,
         int seg_h) {
     extern __shared__ __align__(16) char smem_raw[];
-    const int ys = blockIdx.y * seg_h;
-    strip_body<T, ST, SW, DEPTH>(src, dst, P, blockIdx.x * SW, ys, min(ys + seg_h, P.ny),
-                                 smem_raw);
+    const int ys = P.ya + blockIdx.y * seg_h;
+    strip_body<T, ST, SW, DEPTH, SLAB>(src, dst, P, blockIdx.x * SW, ys, min(ys + seg_h, P.yb),
+                                       smem_raw);
 }
 
 // ---------------------------------------------------------------- batches

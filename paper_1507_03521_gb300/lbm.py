@@ -33,7 +33,10 @@ EXPORTS = ["lbm_version", "lbm_buffer_sizes", "lbm_create", "lbm_bind_buffers", 
            "lbm_batch_autotune", "lbm_batch_fields", "lbm_batch_mass", "lbm_batch_cells",
            "lbm_batch_step_count", "lbm_batch_segment", "lbm_batch_last_error",
            "lbm_batch_destroy", "lbm_adj_work_bytes", "lbm_adj_reset", "lbm_adj_seed",
-           "lbm_adj_step", "lbm_adj_init", "lbm_adj_grads"]
+           "lbm_adj_step", "lbm_adj_init", "lbm_adj_grads",
+           "lbm_slabs_buffer_sizes", "lbm_slabs_create", "lbm_slabs_bind_buffers",
+           "lbm_slabs_scatter", "lbm_slabs_gather", "lbm_slabs_step", "lbm_slabs_rows",
+           "lbm_slabs_step_count", "lbm_slabs_last_error", "lbm_slabs_destroy"]
 
 
 class LBMError(RuntimeError):
@@ -137,6 +140,28 @@ def load(path: str = LIB_PATH):
     lib.lbm_batch_last_error.argtypes = [_vp]
     lib.lbm_batch_destroy.restype = None
     lib.lbm_batch_destroy.argtypes = [_vp]
+    IP = ctypes.POINTER(ctypes.c_int)
+    lib.lbm_slabs_buffer_sizes.restype = S
+    lib.lbm_slabs_buffer_sizes.argtypes = [P, ctypes.c_int, IP, ctypes.POINTER(ctypes.c_size_t),
+                                           ctypes.POINTER(ctypes.c_size_t)]
+    lib.lbm_slabs_create.restype = S
+    lib.lbm_slabs_create.argtypes = [P, ctypes.c_int, IP, _vp, ctypes.POINTER(_vp)]
+    lib.lbm_slabs_bind_buffers.restype = S
+    lib.lbm_slabs_bind_buffers.argtypes = [_vp, _vp, ctypes.c_size_t, _vp, ctypes.c_size_t]
+    lib.lbm_slabs_scatter.restype = S
+    lib.lbm_slabs_scatter.argtypes = [_vp, _vp, ctypes.c_int64]
+    lib.lbm_slabs_gather.restype = S
+    lib.lbm_slabs_gather.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.lbm_slabs_step.restype = S
+    lib.lbm_slabs_step.argtypes = [_vp, ctypes.c_int64]
+    lib.lbm_slabs_rows.restype = S
+    lib.lbm_slabs_rows.argtypes = [_vp, ctypes.c_int, IP, IP]
+    lib.lbm_slabs_step_count.restype = ctypes.c_int64
+    lib.lbm_slabs_step_count.argtypes = [_vp]
+    lib.lbm_slabs_last_error.restype = ctypes.c_char_p
+    lib.lbm_slabs_last_error.argtypes = [_vp]
+    lib.lbm_slabs_destroy.restype = None
+    lib.lbm_slabs_destroy.argtypes = [_vp]
     lib.lbm_adj_work_bytes.restype = S
     lib.lbm_adj_work_bytes.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t)]
     lib.lbm_adj_reset.restype = S
@@ -329,6 +354,92 @@ class Sim:
         self._check(self._lib.lbm_adj_grads(self._h, work.data_ptr(), ctypes.byref(dM),
                                             ctypes.byref(dS)))
         return dM.value, dS.value
+
+
+class Slabs:
+    """One domain as y-slabs stepped separately with device-to-device ghost
+    exchange (``lbm_slabs_*``).  ``n_slabs`` even slabs, or explicit
+    ``row_starts``.  States are whole-domain levels as ``Sim.get_state``
+    returns them; the slabs run on ``stream`` (default: torch's current)."""
+
+    def __init__(self, params: dict, dtype="f32", n_slabs=2, row_starts=None, stream=None,
+                 device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblbm needs a CUDA device; none is available")
+        self._lib = load()
+        self.params = dict(params)
+        self.dtype = dtype
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._cp = make_params(self.params, dtype)
+        if row_starts is not None:
+            n_slabs = len(row_starts)
+            self._starts = (ctypes.c_int * n_slabs)(*[int(r) for r in row_starts])
+        else:
+            self._starts = None
+        self.n = int(n_slabs)
+        sb, wb = ctypes.c_size_t(), ctypes.c_size_t()
+        st = self._lib.lbm_slabs_buffer_sizes(ctypes.byref(self._cp), self.n, self._starts,
+                                              ctypes.byref(sb), ctypes.byref(wb))
+        if st != 0:
+            raise LBMError(st, self._lib.lbm_create_error().decode())
+        h = _vp()
+        st = self._lib.lbm_slabs_create(ctypes.byref(self._cp), self.n, self._starts,
+                                        _vp(self.stream.cuda_stream), ctypes.byref(h))
+        if st != 0:
+            raise LBMError(st, self._lib.lbm_create_error().decode())
+        self._h = h
+        self.state_buf = torch.empty(sb.value, dtype=torch.uint8, device=self.device)
+        self.work_buf = torch.empty(wb.value, dtype=torch.uint8, device=self.device)
+        torch.cuda.synchronize(self.device)
+        self._check(self._lib.lbm_slabs_bind_buffers(h, self.state_buf.data_ptr(), sb.value,
+                                                     self.work_buf.data_ptr(), wb.value))
+
+    def _check(self, st):
+        if st != 0:
+            raise LBMError(st, self._lib.lbm_slabs_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.stream.synchronize()
+            self._lib.lbm_slabs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rows(self):
+        out = []
+        for i in range(self.n):
+            a, b = ctypes.c_int(), ctypes.c_int()
+            self._check(self._lib.lbm_slabs_rows(self._h, i, ctypes.byref(a), ctypes.byref(b)))
+            out.append((a.value, b.value))
+        return out
+
+    @property
+    def step_count(self) -> int:
+        return self._lib.lbm_slabs_step_count(self._h)
+
+    def scatter(self, level, step: int = 0):
+        """Load a whole-domain level (uint8 device tensor)."""
+        self._level_keep = level
+        self._check(self._lib.lbm_slabs_scatter(self._h, level.data_ptr(), int(step)))
+
+    def gather(self, out=None):
+        """The current state as a whole-domain level; returns (tensor, step)."""
+        import torch
+        if out is None:
+            out = torch.zeros_like(self._level_keep)
+        step = ctypes.c_int64()
+        self._check(self._lib.lbm_slabs_gather(self._h, out.data_ptr(), ctypes.byref(step)))
+        return out, step.value
+
+    def step(self, n=1):
+        self._check(self._lib.lbm_slabs_step(self._h, int(n)))
 
 
 class Batch:
