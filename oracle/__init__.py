@@ -41,6 +41,28 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_LIB_OMP = os.path.join(_HERE, "liborc_omp.so")
+
+
+def build_omp(force: bool = False) -> str:
+    """The same source built with OpenMP (``liborc_omp.so``): the passes
+    over cells run on all host cores, bit-identical to ``liborc.so``."""
+    if (not force and os.path.exists(_LIB_OMP)
+            and os.path.getmtime(_LIB_OMP) >= os.path.getmtime(_SRC)):
+        return _LIB_OMP
+    tmp = _LIB_OMP + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fopenmp",
+           "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
+def set_threads(n: int, lib: str | None = None) -> int:
+    """Threads of the OpenMP build's passes (n <= 0: keep); returns the count."""
+    return int(_load(lib).orc_set_threads(int(n)))
+
+
 class _Params(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int), ("ny", ctypes.c_int),
@@ -94,6 +116,8 @@ def _load(path: str | None = None):
     lib.orc_cell_terms.argtypes = [ctypes.c_double] * 16 + [_dp] * 4
     lib.orc_stencils.argtypes = [ctypes.c_int] * 4 + [_dp] * 4
     lib.orc_lattice.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dp]
+    lib.orc_set_threads.restype = ctypes.c_int
+    lib.orc_set_threads.argtypes = [ctypes.c_int]
     _libs[path] = lib
     return lib
 

@@ -57,6 +57,17 @@
 #include <string.h>
 #include <stdio.h>
 
+/* Built with -fopenmp (liborc_omp.so), the passes whose iterations write
+ * disjoint cells run over all host cores; the arithmetic of every cell is
+ * unchanged, so that build is bit-identical to the serial one.  Reductions
+ * (mass, Laplace means) stay serial to keep their summation order. */
+#ifdef _OPENMP
+#include <omp.h>
+#define ORC_PAR_ROWS _Pragma("omp parallel for schedule(static)")
+#else
+#define ORC_PAR_ROWS
+#endif
+
 /* D2Q9 velocities and weights, Sec. 3 (end): c_0 = 0, c_1..4 axis-aligned at
  * angles (i-1)pi/2, c_5..8 diagonal at angles (2i-1)pi/4. */
 static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -199,6 +210,7 @@ static void macroscopic(orc_sim *s) {
     const int nx = s->P.nx, ny = s->P.ny;
     const long N = s->N;
     /* pass 1: phi (Eq. 30), rho (Eq. 11) */
+    ORC_PAR_ROWS
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             long k = idx(s, x, y);
@@ -208,6 +220,7 @@ static void macroscopic(orc_sim *s) {
             s->rho[k] = s->P.rho_B + (acc - s->P.phi_B) * s->drho;
         }
     /* pass 2: chemical potential (Eq. 5) */
+    ORC_PAR_ROWS
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             long k = idx(s, x, y);
@@ -216,6 +229,7 @@ static void macroscopic(orc_sim *s) {
             s->mu[k] = dpsi - ((ORC_MUTANT == 11) ? -1.0 : 1.0) * s->kappa * lap_at(s, s->phi, x, y);
         }
     /* pass 3: gradients */
+    ORC_PAR_ROWS
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             long k = idx(s, x, y);
@@ -226,6 +240,7 @@ static void macroscopic(orc_sim *s) {
             s->lmu[k] = lap_at(s, s->mu, x, y);
         }
     /* pass 4: force, velocity (Eq. 31), pressure (Eq. 32) */
+    ORC_PAR_ROWS
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             long k = idx(s, x, y);
@@ -250,6 +265,7 @@ static void macroscopic(orc_sim *s) {
             s->p[k] = sf + 0.5 * CS2 * (udr - ((ORC_MUTANT == 8) ? 0.0 : 1.0) * s->gamma * rh * s->lambda * s->lmu[k]);
         }
     /* pass 5: pressure gradient */
+    ORC_PAR_ROWS
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             long k = idx(s, x, y);
@@ -260,9 +276,10 @@ static void macroscopic(orc_sim *s) {
 /* Pass 6: collision of Eqs. 22-23. */
 static void collide(orc_sim *s) {
     const long N = s->N;
-    double feq[9], geq[9], Fi[9], Gi[9];
     const double tf = s->P.tau_f, tg = s->P.tau_g;
+    ORC_PAR_ROWS
     for (long k = 0; k < N; ++k) {
+        double feq[9], geq[9], Fi[9], Gi[9];
         cell_terms(s->alpha, s->gamma, s->lambda, s->phi[k], s->mu[k], s->p[k], s->rho[k],
                    s->ux[k], s->uy[k], s->Fx[k], s->Fy[k], s->grhx[k], s->grhy[k],
                    s->lmu[k], s->gpx[k], s->gpy[k], feq, geq, Fi, Gi);
@@ -283,6 +300,7 @@ static void collide(orc_sim *s) {
 static void stream(orc_sim *s) {
     const int nx = s->P.nx, ny = s->P.ny;
     const long N = s->N;
+    ORC_PAR_ROWS
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             long k = idx(s, x, y);
@@ -506,6 +524,18 @@ void orc_set_pops(orc_sim *s, const double *f, const double *g) {
 }
 
 long orc_step_count(const orc_sim *s) { return s->step; }
+
+/* Threads of the OpenMP build (no effect in the serial build); returns the
+ * number the passes will use. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* Unit-test access to the per-cell formulas (Eqs. 24-29). */
 void orc_cell_terms(double alpha, double gamma, double lambda,
