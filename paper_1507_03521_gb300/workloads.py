@@ -166,6 +166,38 @@ def paper_flat(nx=10, ny=100, Pe=50.0, Cn=4.0):
     return p, phi
 
 
+def paper_bubble(nx=160, ny=480, R=32.0, yc=120.0, Pe=50.0, Cn=4.0):
+    """Bubble rising under buoyancy, Sec. 4.3: 160 x 480 periodic, a light
+    bubble of fluid B (phi_B = 0, rho_B = 0.5) of radius 32 in fluid A
+    (phi_A = 1, rho_A = 1); F_b,y = -(rho - rho_A) g with g = 1e-5;
+    tau_f = tau_g = 1, sigma = 1e-3, Pe = 50, Cn = 4 (lambda = 1/(Pe beta)).
+    The paper does not give the bubble's starting point: it is centred in
+    x (x = nx/2, which keeps the lattice mirror x -> nx - x exact) at
+    y = 120, a quarter of the way up."""
+    sigma, W = 1e-3, float(Cn)
+    beta = 12.0 * sigma / W
+    p = _base(nx=nx, ny=ny, rho_A=1.0, rho_B=0.5, phi_A=1.0, phi_B=0.0, sigma=sigma, W=W,
+              M=1.0 / (Pe * beta), tau_f=1.0, tau_g=1.0, gravity=1e-5, rho_ref=1.0)
+    phi = droplet_field(nx, ny, nx / 2.0, yc, R, W, 0.0, 1.0)
+    return p, phi
+
+
+def paper_phase_separation(gamma=1.0, Pe=50.0, Cn=4.0, eps=0.1, n=100):
+    """Phase separation, Sec. 4.4: n x n periodic (100 in the paper),
+    phi = 0.5 [1 + eps sin(4 pi x/Lx) cos(4 pi y/Ly)] with eps = 0.1;
+    rho_A = 1, phi_A = 1, phi_B = 0, tau_f = tau_g = 1, sigma = 1e-3;
+    lambda beta = 1/Pe (0.02 and 0.005), W = Cn (4 and 8), rho_r = 2 and 5,
+    i.e. gamma = rho_r - 1 = 1 and 4 (Eq. 17 with phi_B = 0)."""
+    sigma, W = 1e-3, float(Cn)
+    beta = 12.0 * sigma / W
+    p = _base(nx=n, ny=n, rho_A=1.0, rho_B=1.0 / (1.0 + gamma), phi_A=1.0, phi_B=0.0,
+              sigma=sigma, W=W, M=1.0 / (Pe * beta), tau_f=1.0, tau_g=1.0, rho_ref=1.0)
+    x = np.arange(n, dtype=np.float64)
+    X, Y = np.meshgrid(x, x)
+    phi = 0.5 * (1.0 + eps * np.sin(4 * np.pi * X / n) * np.cos(4 * np.pi * Y / n))
+    return p, phi
+
+
 def small_case(nx, ny, seed, walls=False, gravity=0.0, u_wall=0.0, rho_ratio=10.0):
     """A small seeded domain for parity: an off-centre droplet with a
     seeded velocity perturbation, phi in [-1, 1]."""

@@ -17,7 +17,7 @@ def oracle_spread(p, phi, ux, uy, steps, base):
     rng = np.random.default_rng(12345)
     pert = np.where(rng.uniform(size=phi.shape) < 0.5, np.nextafter(phi, np.inf),
                     np.nextafter(phi, -np.inf))
-    o = oracle.Oracle(p)
+    o = fast_oracle(p)
     o.init_phi(pert, ux, uy)
     o.step(steps)
     f = o.fields()
@@ -31,3 +31,43 @@ def check64(g, o, spread, tag, keys=FIELDS):
         assert err <= tol, f"{tag}: {k} error {err:.3e} > {tol:.3e}"
 
 
+
+
+def fast_oracle(p):
+    """The oracle, from its OpenMP build where the compiler has OpenMP (bit-
+    identical to the serial build), else the serial build."""
+    try:
+        lib = oracle.build_omp()
+    except Exception:
+        return oracle.Oracle(p)
+    import os
+    oracle.set_threads(len(os.sched_getaffinity(0)), lib)
+    return oracle.Oracle(p, lib=lib)
+
+
+def linear_rate(p, phibar, a, b):
+    """Growth rate per step of a small mode of wavenumbers (a, b) about a
+    uniform phibar, from Eq. 19 linearised at u = 0:
+        d phi^/dt = (1 + gamma phibar) lambda L (psi'' - kappa L) phi^,
+    with L the symbol of the isotropic lattice Laplacian,
+        L = (2/cs2) [(2/9)(cos a + cos b) + (1/9) cos a cos b - 5/9],
+    psi'' the second derivative of the double well of Eq. 2 at phibar,
+    kappa and beta from Eqs. 3-4 and gamma from Eq. 17 (lambda = M)."""
+    import math
+    pa, pb = p["phi_A"], p["phi_B"]
+    d = pa - pb
+    kappa = 3.0 * p["sigma"] * p["W"] / (2.0 * d * d)
+    beta = 12.0 * p["sigma"] / (p["W"] * d ** 4)
+    gamma = (p["rho_A"] - p["rho_B"]) / (p["rho_B"] * pa - p["rho_A"] * pb)
+    mid = 0.5 * (pa + pb)
+    # psi' = 4 beta (phi - pa)(phi - pb)(phi - mid)
+    psi2 = 4.0 * beta * ((phibar - pb) * (phibar - mid) + (phibar - pa) * (phibar - mid)
+                         + (phibar - pa) * (phibar - pb))
+    L = 6.0 * ((2.0 / 9.0) * (math.cos(a) + math.cos(b)) + (1.0 / 9.0) * math.cos(a) * math.cos(b)
+               - 5.0 / 9.0)
+    return (1.0 + gamma * phibar) * p["M"] * L * (psi2 - kappa * L)
+
+
+def mode_amplitude(phi, mode):
+    """Projection of phi - mean on a sin*cos mode (normalised: amplitude)."""
+    return float(np.sum((phi - phi.mean()) * mode) / np.sum(mode * mode))
