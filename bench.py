@@ -269,7 +269,8 @@ def measure_batch(lbm, W, args, peak, dist):
             "mlups": round(cells * args.steps * world / (ms * 1e-3) / 1e6, 2),
             "ms_per_step": round(ms / args.steps, 5), "hbm_gbs": round(gbs, 1),
             "frac": round(gbs / peak, 4), "seg_h": seg, "graph": True,
-            "launches_per_step": 1, "kernel": "k_strip_batch<float>"}
+            "launches_per_step": 1, "kernel": "k_strip_batch<float>",
+            "traffic": _traffic("batch_f32"), "bytes_alg": BYTES_PER_CELL["f32"] * cells}
 
 
 def measure_slabs(lbm, p, phi, args, mlups_single, dist, n_slabs=4):
@@ -304,7 +305,8 @@ def measure_slabs(lbm, p, phi, args, mlups_single, dist, n_slabs=4):
     sl.close()
     return {"n_slabs": n_slabs, "mlups": round(mlups, 2), "ms_per_step": round(ms / args.steps, 5),
             "vs_whole_domain": round(mlups / mlups_single, 4),
-            "launches_per_step": n_slabs + 2, "exchange_bytes_per_step": exch}
+            "launches_per_step": n_slabs + 2, "exchange_bytes_per_step": exch,
+            "slab_kernel_traffic": _traffic("slab_f32")}
 
 
 def measure_adjoint(W):
