@@ -116,6 +116,7 @@ def _load(path: str | None = None):
     lib.orc_cell_terms.argtypes = [ctypes.c_double] * 16 + [_dp] * 4
     lib.orc_stencils.argtypes = [ctypes.c_int] * 4 + [_dp] * 4
     lib.orc_lattice.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dp]
+    lib.orc_set_gradp_lag.argtypes = [ctypes.c_void_p, ctypes.c_int]
     lib.orc_set_threads.restype = ctypes.c_int
     lib.orc_set_threads.argtypes = [ctypes.c_int]
     _libs[path] = lib
@@ -169,8 +170,9 @@ def params_ok(p: Params) -> bool:
 class Oracle:
     """One FP64 domain stepped by the literal multi-pass scheme."""
 
-    def __init__(self, p: Params | dict, lib: str | None = None):
+    def __init__(self, p: Params | dict, lib: str | None = None, gradp_lag: bool = False):
         if isinstance(p, dict):
+            gradp_lag = bool(p.get("gradp_lag", gradp_lag))
             p = params_from_dict(p)
         self.p = p
         self._lib = _load(lib)
@@ -179,6 +181,7 @@ class Oracle:
         if not h:
             raise ValueError(f"oracle rejected parameters {p}")
         self._h = ctypes.c_void_p(h)
+        self._lib.orc_set_gradp_lag(self._h, int(gradp_lag))
         self.shape = (p.ny, p.nx)
 
     def close(self):

@@ -100,6 +100,9 @@ typedef struct {
     /* macroscopic fields of the current time level (passes 1-5) */
     double *phi, *rho, *mu, *gphx, *gphy, *grhx, *grhy, *gmux, *gmuy, *lmu;
     double *Fx, *Fy, *ux, *uy, *p, *gpx, *gpy;
+    /* lagged variant: grad p in G_i from the previous step's p (pprev) */
+    int lag;
+    double *pprev;
     long step;
 } orc_sim;
 
@@ -264,12 +267,14 @@ static void macroscopic(orc_sim *s) {
             s->uy[k] = uy;
             s->p[k] = sf + 0.5 * CS2 * (udr - ((ORC_MUTANT == 8) ? 0.0 : 1.0) * s->gamma * rh * s->lambda * s->lmu[k]);
         }
-    /* pass 5: pressure gradient */
+    /* pass 5: pressure gradient (of the previous step's p in the lagged
+     * variant) */
+    const double *pg = s->lag ? s->pprev : s->p;
     ORC_PAR_ROWS
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             long k = idx(s, x, y);
-            grad_at(s, s->p, x, y, 1, &s->gpx[k], &s->gpy[k]);
+            grad_at(s, pg, x, y, 1, &s->gpx[k], &s->gpy[k]);
         }
 }
 
@@ -369,10 +374,10 @@ orc_sim *orc_create(const orc_params *P) {
         *bufs9[b] = (double *)calloc((size_t)(9 * N), sizeof(double));
         if (!*bufs9[b]) return NULL;
     }
-    double **flds[17] = {&s->phi, &s->rho, &s->mu, &s->gphx, &s->gphy, &s->grhx, &s->grhy,
+    double **flds[18] = {&s->phi, &s->rho, &s->mu, &s->gphx, &s->gphy, &s->grhx, &s->grhy,
                          &s->gmux, &s->gmuy, &s->lmu, &s->Fx, &s->Fy, &s->ux, &s->uy,
-                         &s->p, &s->gpx, &s->gpy};
-    for (int b = 0; b < 17; ++b) {
+                         &s->p, &s->gpx, &s->gpy, &s->pprev};
+    for (int b = 0; b < 18; ++b) {
         *flds[b] = (double *)calloc((size_t)N, sizeof(double));
         if (!*flds[b]) return NULL;
     }
@@ -381,10 +386,10 @@ orc_sim *orc_create(const orc_params *P) {
 
 void orc_destroy(orc_sim *s) {
     if (!s) return;
-    double *all[21] = {s->f, s->g, s->fs, s->gs, s->phi, s->rho, s->mu, s->gphx, s->gphy,
+    double *all[22] = {s->f, s->g, s->fs, s->gs, s->phi, s->rho, s->mu, s->gphx, s->gphy,
                        s->grhx, s->grhy, s->gmux, s->gmuy, s->lmu, s->Fx, s->Fy, s->ux,
-                       s->uy, s->p, s->gpx, s->gpy};
-    for (int b = 0; b < 21; ++b) free(all[b]);
+                       s->uy, s->p, s->gpx, s->gpy, s->pprev};
+    for (int b = 0; b < 22; ++b) free(all[b]);
     free(s);
 }
 
@@ -425,6 +430,7 @@ int orc_init_phi(orc_sim *s, const double *phi0, const double *ux0, const double
             s->g[i * N + k] = H + WT[i] * s->phi[k] * si;
         }
     }
+    memset(s->pprev, 0, (size_t)N * sizeof(double));  /* the initial state's p */
     s->step = 0;
     return 0;
 }
@@ -434,9 +440,17 @@ void orc_step(orc_sim *s, long n) {
         macroscopic(s);
         collide(s);
         stream(s);
+        if (s->lag) memcpy(s->pprev, s->p, (size_t)s->N * sizeof(double));
         s->step++;
     }
 }
+
+/* The lagged-grad-p variant (not in the paper; a measurement of what
+ * synchrony costs): G_i of Eq. 29 takes grad p from the pressure of the
+ * previous step instead of the current one, which makes the step reach 2
+ * cells instead of 3.  Before the first step that pressure is the initial
+ * state's, p = 0.  Set before orc_init_phi. */
+void orc_set_gradp_lag(orc_sim *s, int on) { s->lag = on ? 1 : 0; }
 
 /* Macroscopic fields of the current time level; any pointer may be NULL. */
 void orc_fields(orc_sim *s, double *phi, double *rho, double *p, double *ux, double *uy,
