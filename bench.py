@@ -52,8 +52,8 @@ def _peaks():
 
 
 # Sources that define the step kernels (k_strip, k_step) and their launch.
-STEP_SOURCES = ("lbm_internal.h", "lbm_kernels.cuh", "lbm_strip.cuh", "lbm_ops.cuh",
-                "lbm_f64.cu", "lbm_f32.cu", "lbm_f16.cu")
+STEP_SOURCES = ("lbm_internal.h", "lbm_kernels.cuh", "lbm_strip.cuh", "lbm_strip_lag.cuh",
+                "lbm_ops.cuh", "lbm_f64.cu", "lbm_f32.cu", "lbm_f16.cu")
 
 
 def _kernel_hash() -> str:
@@ -309,6 +309,42 @@ def measure_slabs(lbm, p, phi, args, mlups_single, dist, n_slabs=4):
             "slab_kernel_traffic": _traffic("slab_f32")}
 
 
+def measure_lagged(lbm, p, phi, args, peak, mlups_sync, dist):
+    """The lagged-grad-p variant (grad p in G_i from the previous step's
+    pressure; not the paper's scheme) on the same FP32 workload: its speed
+    against the synchronous step, its roofline (144 B of populations plus
+    4 B of stored pressure read and 4 B written per cell), and how far it
+    drifts from the synchronous step over the run (max-abs phi, u, p)."""
+    import torch
+    q = dict(p, gradp_lag=1)
+    sim = lbm.Sim(q, "f32")
+    sim.init_phi(phi)
+    if dist is not None:
+        torch.cuda.synchronize()
+        dist.barrier()
+    total, per = time_steps(sim, args.steps, args.warmup)
+    total = max_over_ranks(total, dist, "cuda")
+    world = dist.get_world_size() if dist is not None else 1
+    cells = p["nx"] * p["ny"]
+    mlups = cells * args.steps * world / (total * 1e-3) / 1e6
+    bpc = BYTES_PER_CELL["f32"] + 8
+    gbs = bpc * cells / (statistics.mean(per) * 1e-3) / 1e9
+    lag_fields = sim.fields(("phi", "ux", "uy", "p"))
+    sim.close()
+    ref = lbm.Sim(p, "f32")
+    ref.init_phi(phi)
+    ref.step(args.steps + args.warmup)
+    sync_fields = ref.fields(("phi", "ux", "uy", "p"))
+    ref.close()
+    diff = {k: float((lag_fields[k].double() - sync_fields[k].double()).abs().max().item())
+            for k in lag_fields}
+    return {"mlups": round(mlups, 2), "ms_per_step": round(total / args.steps, 5),
+            "vs_synchronous": round(mlups / mlups_sync, 4), "bytes_per_cell": bpc,
+            "hbm_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+            "traffic": _traffic("lag_f32"), "kernel": "k_strip_lag<float>",
+            "max_abs_diff_vs_synchronous": diff, "steps_for_diff": args.steps + args.warmup}
+
+
 def measure_adjoint(W):
     """Adjoint workload: droplet in shear, 512 x 512, R = 64, walls at
     +-0.01, rho ratio 10, FP32, 4000 steps, checkpoints every 200 steps;
@@ -357,6 +393,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
     ap.add_argument("--no-slabs", action="store_true", help="skip the y-slab decomposition")
+    ap.add_argument("--no-lagged", action="store_true", help="skip the lagged-grad-p variant")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -466,6 +503,8 @@ def main():
         line["batched"] = measure_batch(lbm, W, args, peak, dist)
     if not args.no_slabs:
         line["slabs"] = measure_slabs(lbm, p, phi, args, mlups, dist)
+    if not args.no_lagged:
+        line["gradp_lag"] = measure_lagged(lbm, p, phi, args, peak, mlups, dist)
     if not args.no_adjoint:
         line["adjoint"] = measure_adjoint(W)
 

@@ -83,7 +83,13 @@ typedef enum { LBM_PERIODIC = 0, LBM_WALL = 1 } lbm_bc;
  *   bc_y            LBM_PERIODIC, or LBM_WALL: no-slip walls at y = -1/2
  *                   and y = ny - 1/2 (halfway bounce-back)
  *   u_wall_bottom, u_wall_top  x-velocity of the walls (LBM_WALL only)
- *   dtype           an lbm_dtype */
+ *   dtype           an lbm_dtype
+ *   gradp_lag       0: the paper's synchronous step (default).  1: the
+ *                   lagged-grad-p variant, not in the paper: G_i of Eq. 29
+ *                   takes grad p from the previous step's pressure (0
+ *                   before the first step), which each level then stores
+ *                   in one more slot.  Single domains with nx a multiple of
+ *                   8 only (not batches, slabs or the adjoint). */
 typedef struct {
     int nx, ny;
     double rho_A, rho_B, phi_A, phi_B;
@@ -92,6 +98,7 @@ typedef struct {
     int bc_x, bc_y;
     double u_wall_bottom, u_wall_top;
     int dtype;
+    int gradp_lag;
 } lbm_params;
 
 /* Library ABI version (this header: 1). */

@@ -30,9 +30,17 @@ struct Layout {
     size_t level, state, field_slot, part_off, out_off, work;
 };
 
+// The lagged variant's P slot follows the populations of a level.
+size_t p_slot_offset(const Derived &d, const Ops *ops) { return round256(ops->level_bytes(d.NS)); }
+
+// Bytes of one time level as get/set_state copy it.
+size_t level_state_bytes(const Derived &d, const Ops *ops) {
+    return d.lag ? p_slot_offset(d, ops) + (size_t)d.NS * ops->field_size : ops->level_bytes(d.NS);
+}
+
 Layout layout(const Derived &d, const Ops *ops) {
     Layout L;
-    L.level = round256(ops->level_bytes(d.NS));
+    L.level = round256(level_state_bytes(d, ops));
     L.state = 2 * L.level;
     L.field_slot = round256((size_t)d.NS * ops->field_size);
     L.part_off = kFieldSlots * L.field_slot;
@@ -71,6 +79,8 @@ std::string check_params(const lbm_params *p) {
     if (p->bc_x != LBM_PERIODIC) return "bc_x must be LBM_PERIODIC";
     if (p->bc_y != LBM_PERIODIC && p->bc_y != LBM_WALL) return "bc_y must be LBM_PERIODIC or LBM_WALL";
     if (!ops_for(p->dtype)) return "unknown dtype";
+    if (p->gradp_lag != 0 && p->gradp_lag != 1) return "gradp_lag must be 0 or 1";
+    if (p->gradp_lag && p->nx % 8 != 0) return "the lagged-grad-p variant needs nx a multiple of 8";
     const double vals[] = {p->rho_A, p->rho_B, p->phi_A, p->phi_B, p->sigma, p->W, p->M,
                            p->tau_f, p->tau_g, p->gravity, p->rho_ref, p->u_wall_bottom,
                            p->u_wall_top};
@@ -91,6 +101,7 @@ Derived derive(const lbm_params *p) {
     d.rows = d.ny;
     d.ya = 0;
     d.yb = d.ny;
+    d.lag = p->gradp_lag ? 1 : 0;
     const double dphi = p->phi_A - p->phi_B;
     d.phiA = p->phi_A;
     d.phiB = p->phi_B;
@@ -205,6 +216,11 @@ lbm_status lbm_create(const lbm_params *prm, void *stream, lbm_sim **out) {
     s->prm = *prm;
     s->d = derive(prm);
     s->ops = ops_for(prm->dtype);
+    if (s->d.lag && !s->ops->strip_ok(s->d)) {
+        delete s;
+        g_create_err = "the lagged-grad-p variant needs the strip form (grid too large)";
+        return LBM_ERR_ARG;
+    }
     s->L = layout(s->d, s->ops);
     s->stream = static_cast<cudaStream_t>(stream);
     g_create_err.clear();
@@ -246,6 +262,9 @@ lbm_status lbm_init_phi(lbm_sim *s, const void *phi, const void *ux, const void 
     }
     s->cur = 0;
     LBM_CK(s, s->ops->init(s->d, dphi, dux, duy, s->level(0), s->stream));
+    if (s->d.lag)  // the previous-step pressure of the initial state: p = 0
+        LBM_CK(s, cudaMemsetAsync(s->level(0) + p_slot_offset(s->d, s->ops), 0,
+                                  (size_t)s->d.NS * s->ops->field_size, s->stream));
     if (on_host) LBM_CK(s, cudaStreamSynchronize(s->stream));
     s->steps = 0;
     s->initialized = true;
@@ -323,7 +342,7 @@ lbm_status lbm_laplace(lbm_sim *s, double xc, double yc, double R, double *dP, d
     return LBM_OK;
 }
 
-size_t lbm_state_bytes(const lbm_sim *s) { return s ? s->ops->level_bytes(s->d.NS) : 0; }
+size_t lbm_state_bytes(const lbm_sim *s) { return s ? level_state_bytes(s->d, s->ops) : 0; }
 
 lbm_status lbm_get_state(lbm_sim *s, void *dst, int on_host, int64_t *step) {
     if (!s) return LBM_ERR_ARG;
@@ -375,6 +394,7 @@ static lbm::AdjHost adj_host(const lbm_params &p) {
 static lbm_status adj_ready(lbm_sim *s, const void *work) {
     if (!s) return LBM_ERR_ARG;
     if (!s->ops->adj_step) return s->fail(LBM_ERR_ARG, "the adjoint needs LBM_F64 or LBM_F32");
+    if (s->d.lag) return s->fail(LBM_ERR_ARG, "the adjoint is of the synchronous step (gradp_lag = 0)");
     if (!work) return s->fail(LBM_ERR_ARG, "null adjoint work buffer");
     if (reinterpret_cast<uintptr_t>(work) & 255)
         return s->fail(LBM_ERR_ARG, "adjoint work buffer must be 256-byte aligned");
@@ -383,7 +403,7 @@ static lbm_status adj_ready(lbm_sim *s, const void *work) {
 
 lbm_status lbm_adj_work_bytes(const lbm_sim *s, size_t *bytes) {
     if (!s || !bytes) return LBM_ERR_ARG;
-    if (!s->ops->adj_step) return LBM_ERR_ARG;
+    if (!s->ops->adj_step || s->d.lag) return LBM_ERR_ARG;
     *bytes = lbm::adj_work_bytes(s->d.NS, s->ops->field_size);
     return LBM_OK;
 }

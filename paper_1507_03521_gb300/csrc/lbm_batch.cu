@@ -51,6 +51,7 @@ std::string make_plan(const lbm_params *prms, int n, Plan &P, const Ops **ops_ou
         if (lbm_buffer_sizes(&prms[i], &sb, &wb) != LBM_OK)
             return "domain " + std::to_string(i) + ": " + lbm_create_error();
         if (prms[i].dtype != prms[0].dtype) return "all domains of a batch share one dtype";
+        if (prms[i].gradp_lag) return "batched domains take the synchronous step (gradp_lag = 0)";
         Derived d = derive(&prms[i]);
         if (!ops->strip_ok(d))
             return "domain " + std::to_string(i) + ": batched domains need nx a multiple of 8";

@@ -18,6 +18,7 @@ struct Derived {
     // rows held and stepped by the strip kernel (KP in lbm_kernels.cuh):
     // the whole domain, or one y-slab of a decomposed domain
     int slab, y0, rows, ya, yb;
+    int lag;  // lagged-grad-p variant (its level carries a P slot)
     double phiA, phiB, phibar, rhoB, drho;
     double kappa, beta, alpha, lambda, gamma;
     double grav, rhoref, tau_f, tau_g, uwb, uwt;

@@ -8,6 +8,7 @@
 #include "lbm_adjoint.cuh"
 #include "lbm_kernels.cuh"
 #include "lbm_strip.cuh"
+#include "lbm_strip_lag.cuh"
 
 namespace lbm {
 
@@ -107,6 +108,42 @@ struct OpsImpl {
         return cudaGetLastError();
     }
 
+    // The lagged-grad-p variant (strip form only; the level carries a P slot
+    // after the populations).
+    using LS = LagSmem<T, ST, SW, DEPTH>;
+    static size_t p_offset(long long NS) { return (ST::level_bytes(NS) + 255) & ~size_t(255); }
+    static cudaError_t lag_step(const Derived &d, const void *src, void *dst, cudaStream_t s) {
+        static StripCfg cfg[64];
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev >= 64) return cudaErrorInvalidDevice;
+        StripCfg &c = cfg[dev];
+        if (!c.ready) {
+            e = cudaFuncSetAttribute(k_strip_lag<T, ST, SW, DEPTH>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LS::bytes);
+            if (e != cudaSuccess) return e;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.per_sm, k_strip_lag<T, ST, SW, DEPTH>,
+                                                              SW, LS::bytes);
+            if (e != cudaSuccess) return e;
+            e = cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+            if (c.per_sm < 1) return cudaErrorInvalidConfiguration;
+            c.ready = true;
+        }
+        const int strips = (d.nx + SW - 1) / SW;
+        long long nseg = (long long)c.per_sm * c.sms / strips;
+        if (nseg < 1) nseg = 1;
+        const long long max_seg = (d.ny + 15) / 16;
+        if (nseg > max_seg) nseg = max_seg;
+        const int seg_h = (int)((d.ny + nseg - 1) / nseg);
+        nseg = (d.ny + seg_h - 1) / seg_h;
+        k_strip_lag<T, ST, SW, DEPTH><<<dim3((unsigned)strips, (unsigned)nseg), SW, LS::bytes, s>>>(
+            static_cast<const char *>(src), static_cast<char *>(dst), make_kp<T>(d),
+            (long long)p_offset(d.NS), seg_h);
+        return cudaGetLastError();
+    }
+
     template <int MODE>
     static cudaError_t prepare() {
         // Opt in to more than 48 KB of dynamic shared memory when needed,
@@ -128,7 +165,9 @@ struct OpsImpl {
     }
 
     static cudaError_t step(const Derived &d, const void *src, void *dst, cudaStream_t s) {
-        // a y-slab (lbm_slabs.cu) has been checked for the strip form
+        // a y-slab (lbm_slabs.cu) and the lagged variant have been checked
+        // for the strip form
+        if (d.lag) return strip_ok(d) ? lag_step(d, src, dst, s) : cudaErrorInvalidValue;
         if (d.slab) return strip_ok(d) ? strip_step<true>(d, src, dst, s) : cudaErrorInvalidValue;
         if (strip_ok(d)) return strip_step<false>(d, src, dst, s);
         cudaError_t e = prepare<MODE_STEP>();

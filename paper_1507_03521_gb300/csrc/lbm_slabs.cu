@@ -72,6 +72,7 @@ struct Plan {
 std::string make_plan(const lbm_params *p, int n, const int *starts, Plan &P, const Ops **ops_out) {
     std::string m = lbm::check_params(p);
     if (!m.empty()) return m;
+    if (p->gradp_lag) return "slabs take the synchronous step (gradp_lag = 0)";
     const Ops *ops = lbm::ops_for(p->dtype);
     P.d = lbm::derive(p);
     if (n < 1) return "need at least one slab";

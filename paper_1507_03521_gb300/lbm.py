@@ -57,6 +57,7 @@ class CParams(ctypes.Structure):
         ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
         ("u_wall_bottom", ctypes.c_double), ("u_wall_top", ctypes.c_double),
         ("dtype", ctypes.c_int),
+        ("gradp_lag", ctypes.c_int),
     ]
 
 
@@ -182,8 +183,8 @@ def make_params(d: dict, dtype) -> CParams:
     """lbm_params from a parameter dict in the paper's notation."""
     if isinstance(dtype, str):
         dtype = DTYPES[dtype]
-    keys = [f[0] for f in CParams._fields_ if f[0] != "dtype"]
-    return CParams(*[d[k] for k in keys], dtype)
+    keys = [f[0] for f in CParams._fields_ if f[0] not in ("dtype", "gradp_lag")]
+    return CParams(*[d[k] for k in keys], dtype, int(d.get("gradp_lag", 0)))
 
 
 def buffer_sizes(d: dict, dtype):
