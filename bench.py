@@ -195,7 +195,7 @@ def cpu_baseline():
            "sample": f"{sample}, {CPU_SAMPLE_STEPS} steps, {dts:.1f} s, FP64, serial build"}
     lib, threads = _oracle_omp()
     if lib is not None and threads > 1:
-        steps = CPU_SAMPLE_STEPS * 4
+        steps = CPU_SAMPLE_STEPS * 12
         par, dtp = run(lib, steps)
         out = {"value": round(par, 4), "unit": "MLUPS", "cores": threads, "kind": "oracle",
                "sample": f"{sample}, {steps} steps, {dtp:.1f} s, FP64, OpenMP build "

@@ -1,8 +1,15 @@
 // 16-bit storage instantiations: FP32 arithmetic, f_0..8 and g_1..8 stored
-// as FP16 (scaled) or BF16, g_0 in FP32.
+// as FP16 (scaled) or BF16, g_0 in FP32.  Single domains and slabs run
+// 120-column strips on 128 threads; batches run 128-column strips.
 #include "lbm_ops.cuh"
 
 namespace lbm {
-const Ops *ops_f16s() { return OpsImpl<float, Store16<__half>, 2, 128, 2>::ops("f16s"); }
-const Ops *ops_bf16s() { return OpsImpl<float, Store16<__nv_bfloat16>, 2, 128, 2>::ops("bf16s"); }
+const Ops *ops_f16s() {
+    using Batch = OpsImpl<float, Store16<__half>, 2, 128, 2>;
+    return OpsImpl<float, Store16<__half>, 2, 120, 2>::ops_batch_from<Batch>("f16s");
+}
+const Ops *ops_bf16s() {
+    using Batch = OpsImpl<float, Store16<__nv_bfloat16>, 2, 128, 2>;
+    return OpsImpl<float, Store16<__nv_bfloat16>, 2, 120, 2>::ops_batch_from<Batch>("bf16s");
+}
 }  // namespace lbm

@@ -1,6 +1,11 @@
-// FP32 instantiation: populations and arithmetic in FP32.
+// FP32 instantiation: populations and arithmetic in FP32.  Single domains
+// and slabs run 120-column strips on 128 threads (every step of a row in
+// one pass); batches run 128-column strips.
 #include "lbm_ops.cuh"
 
 namespace lbm {
-const Ops *ops_f32() { return OpsImpl<float, PlainStore<float>, 2, 128, 1>::ops("f32"); }
+const Ops *ops_f32() {
+    using Batch = OpsImpl<float, PlainStore<float>, 2, 128, 1>;
+    return OpsImpl<float, PlainStore<float>, 2, 120, 1>::ops_batch_from<Batch>("f32");
+}
 }  // namespace lbm

@@ -48,6 +48,7 @@ inline KP<T> make_kp(const Derived &d) {
 template <class T, class ST, int RPT, int SW, int DEPTH>
 struct OpsImpl {
     static constexpr int TY = 8 * RPT;
+    static constexpr int NT = strip_threads(SW);  // threads of a strip CTA
     using TL = Tile<T, TY>;
     using SM = StripSmem<T, ST, SW, DEPTH>;
 
@@ -77,7 +78,7 @@ struct OpsImpl {
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
             if (e != cudaSuccess) return e;
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &c.per_sm, k_strip<T, ST, SW, DEPTH, SLAB>, SW, SM::bytes);
+                &c.per_sm, k_strip<T, ST, SW, DEPTH, SLAB>, NT, SM::bytes);
             if (e != cudaSuccess) return e;
             e = cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
             if (e != cudaSuccess) return e;
@@ -103,7 +104,7 @@ struct OpsImpl {
         int seg_h = 0;
         cudaError_t e = strip_grid<SLAB>(d, grid, seg_h);
         if (e != cudaSuccess) return e;
-        k_strip<T, ST, SW, DEPTH, SLAB><<<grid, SW, SM::bytes, s>>>(
+        k_strip<T, ST, SW, DEPTH, SLAB><<<grid, NT, SM::bytes, s>>>(
             static_cast<const char *>(src), static_cast<char *>(dst), make_kp<T>(d), seg_h);
         return cudaGetLastError();
     }
@@ -124,7 +125,7 @@ struct OpsImpl {
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LS::bytes);
             if (e != cudaSuccess) return e;
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.per_sm, k_strip_lag<T, ST, SW, DEPTH>,
-                                                              SW, LS::bytes);
+                                                              NT, LS::bytes);
             if (e != cudaSuccess) return e;
             e = cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
             if (e != cudaSuccess) return e;
@@ -138,7 +139,7 @@ struct OpsImpl {
         if (nseg > max_seg) nseg = max_seg;
         const int seg_h = (int)((d.ny + nseg - 1) / nseg);
         nseg = (d.ny + seg_h - 1) / seg_h;
-        k_strip_lag<T, ST, SW, DEPTH><<<dim3((unsigned)strips, (unsigned)nseg), SW, LS::bytes, s>>>(
+        k_strip_lag<T, ST, SW, DEPTH><<<dim3((unsigned)strips, (unsigned)nseg), NT, LS::bytes, s>>>(
             static_cast<const char *>(src), static_cast<char *>(dst), make_kp<T>(d),
             (long long)p_offset(d.NS), seg_h);
         return cudaGetLastError();
@@ -241,7 +242,7 @@ struct OpsImpl {
             if (e != cudaSuccess) return e;
             int per_sm = 0, sms = 0;
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_strip_batch<T, ST, SW, DEPTH>,
-                                                              SW, SM::bytes);
+                                                              NT, SM::bytes);
             if (e != cudaSuccess) return e;
             e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             if (e != cudaSuccess) return e;
@@ -257,7 +258,7 @@ struct OpsImpl {
         int slots = 0;
         cudaError_t e = batch_slots(&slots);  // also sets the shared-memory attribute
         if (e != cudaSuccess) return e;
-        k_strip_batch<T, ST, SW, DEPTH><<<grid, SW, SM::bytes, s>>>(
+        k_strip_batch<T, ST, SW, DEPTH><<<grid, NT, SM::bytes, s>>>(
             state, static_cast<const BatchDom<T> *>(doms), items, nitems, parity);
         return cudaGetLastError();
     }
@@ -333,14 +334,31 @@ struct OpsImpl {
         return cudaGetLastError();
     }
 
+    static constexpr int kSW = SW;
+
+    // The launcher table; the batched form's launchers come from B, which
+    // may be this type at another strip width.
+    template <class B>
+    static Ops table(const char *name) {
+        return Ops{name,        sizeof(T),   &level_bytes, &ST::slot_span,
+                   &step,       &fields,     &init,        &mass,
+                   &laplace,    B::kSW,      &strip_ok,    sizeof(BatchDom<T>),
+                   &B::batch_fill_dom,       &B::batch_slots,   &B::batch_step,
+                   kPlain ? &adj_seed : nullptr, kPlain ? &adj_step : nullptr,
+                   kPlain ? &adj_init : nullptr};
+    }
     static const Ops *ops(const char *name) {
-        static const Ops o = {name,           sizeof(T),      &level_bytes,      &ST::slot_span,
-                              &step,
-                              &fields,        &init,          &mass,             &laplace,
-                              SW,             &strip_ok,      sizeof(BatchDom<T>), &batch_fill_dom,
-                              &batch_slots,   &batch_step,
-                              kPlain ? &adj_seed : nullptr, kPlain ? &adj_step : nullptr,
-                              kPlain ? &adj_init : nullptr};
+        static const Ops o = table<OpsImpl>(name);
+        return &o;
+    }
+    // Single domains and slabs at this strip width, batches at B's.  The
+    // batch's domains have widths that are multiples of 32, which whole-warp
+    // strips tile exactly; a strip width chosen for single pass per step
+    // (not a multiple of 32) would leave a narrow remainder strip in most
+    // of them.
+    template <class B>
+    static const Ops *ops_batch_from(const char *name) {
+        static const Ops o = table<B>(name);
         return &o;
     }
 };

@@ -54,6 +54,14 @@ __device__ __forceinline__ int wrap_any(int x, int nx) {
 __device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
 
+// Threads of a strip CTA of SW columns: SW itself when SW is a multiple of
+// the warp size (each step's halo columns then take an extra pass of one
+// warp), otherwise enough whole warps to cover SW + 6 columns, so that every
+// step (at most 3 halo columns per side) is a single pass.
+__host__ __device__ constexpr int strip_threads(int SW) {
+    return SW % 32 == 0 ? SW : (SW + 6 + 31) / 32 * 32;
+}
+
 // Shared-memory row buffers of the populations, per storage type.  A row
 // buffer holds columns x0-HP .. x0+SW+HP-1 of every slot; the async copy of
 // a row is described once per thread (which 16-byte chunks it copies) and
@@ -69,7 +77,8 @@ struct StripRow<PlainStore<T>, SW> {
     static constexpr int CE = 16 / sizeof(T);  // elements per 16-byte chunk
     static constexpr int CPS = LW / CE;        // chunks per slot
     static constexpr int TOTAL = 9 * CPS;      // chunks of one f row (or g row)
-    static constexpr int NCH = (TOTAL + SW - 1) / SW;
+    static constexpr int NT = strip_threads(SW);
+    static constexpr int NCH = (TOTAL + NT - 1) / NT;
     static constexpr size_t fbytes = (size_t)9 * LW * sizeof(T);  // f_0..f_8
     static constexpr size_t gbytes = (size_t)9 * LW * sizeof(T);  // g_0..g_8
     static bool idx32_ok(long long NS) { return 18 * NS < (1LL << 31); }
@@ -87,7 +96,7 @@ struct StripRow<PlainStore<T>, SW> {
         d.gslot = 9 * (int)NS;
 #pragma unroll
         for (int k = 0; k < NCH; ++k) {
-            const int j = t + k * SW;
+            const int j = t + k * NT;
             const int c0 = (j % CPS) * CE;
             if (j < TOTAL && c0 < need) {
                 const int sl = j / CPS, c = j - sl * CPS;
@@ -146,7 +155,8 @@ struct StripRow<Store16<H>, SW> {
     static constexpr int CH = LW / 8, C0 = LW / 4;  // chunks per half slot, of the g_0 row
     static constexpr int TF = 9 * CH;               // f row: half slots 0..8
     static constexpr int TG = C0 + 8 * CH;          // g row: g_0 floats, half slots 9..16
-    static constexpr int NF = (TF + SW - 1) / SW, NG = (TG + SW - 1) / SW;
+    static constexpr int NT = strip_threads(SW);
+    static constexpr int NF = (TF + NT - 1) / NT, NG = (TG + NT - 1) / NT;
     static constexpr size_t fbytes = (size_t)9 * LW * 2;
     static constexpr size_t gbytes = (size_t)LW * 4 + (size_t)8 * LW * 2;
     // offsets count halves from the level base: half slot s starts at half
@@ -163,7 +173,7 @@ struct StripRow<Store16<H>, SW> {
         const int ns = (int)NS;
 #pragma unroll
         for (int k = 0; k < NF; ++k) {
-            const int j = t + k * SW;
+            const int j = t + k * NT;
             if (j < TF && (j % CH) * 8 < need) {
                 const int sl = j / CH, c = j - sl * CH;
                 d.foff[k] = (2 + sl) * ns + wrap_any(x_start + c * 8, nx);
@@ -176,7 +186,7 @@ struct StripRow<Store16<H>, SW> {
         d.gflt = 0;
 #pragma unroll
         for (int k = 0; k < NG; ++k) {
-            const int j = t + k * SW;
+            const int j = t + k * NT;
             if (j < C0 && j * 4 < need) {
                 d.goff[k] = wrap_any(x_start + j * 4, nx);
                 d.gso[k] = j * 16;  // bytes
@@ -323,9 +333,13 @@ __device__ __forceinline__ int buf_row(const KP<T> &P, int y) {
 // `xw` (a different warp per step), so no warp carries every extra pass.
 template <int SW, int H, int XW, class F>
 __device__ __forceinline__ void columns(int t, F &&fn) {
-    fn(t - H);
-    constexpr int NW = SW / 32;
-    if ((t >> 5) == (XW % NW) && (t & 31) < 2 * H) fn(SW - H + (t & 31));
+    if constexpr (strip_threads(SW) >= SW + 2 * H) {
+        if (t < SW + 2 * H) fn(t - H);  // one pass
+    } else {
+        fn(t - H);
+        constexpr int NW = SW / 32;
+        if ((t >> 5) == (XW % NW) && (t & 31) < 2 * H) fn(SW - H + (t & 31));
+    }
 }
 
 // What the collision of one cell needs (Eqs. 22-29): phi, mu, p, rho,
@@ -592,9 +606,14 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
                         n_gy = gphy;
                     }
                 };
-                if (t < SW) point(t, true);
-                // halo columns -1 and SW: two lanes of the last warp
-                if (t >= SW - 32 && t < SW - 30) point(t == SW - 32 ? -1 : SW, false);
+                if constexpr (strip_threads(SW) >= SW + 2) {
+                    // one pass: thread t takes column t - 1 (and collides it)
+                    if (t < SW + 2) point(t - 1, t >= 1 && t <= SW);
+                } else {
+                    if (t < SW) point(t, true);
+                    // halo columns -1 and SW: two lanes of the last warp
+                    if (t >= SW - 32 && t < SW - 30) point(t == SW - 32 ? -1 : SW, false);
+                }
             } else if (r == ny) {
                 // ghost row above the top wall: linear extrapolation of p
                 const T *p1 = atT(R.p[1]), *p2 = atT(R.p[0]);  // rows ny-1, ny-2
@@ -603,11 +622,13 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
         }
         __syncthreads();
 
-        // 5. collide row y and push (Eqs. 22-29, Gamma_i = 1 + s_i)
+        // 5. collide row y and push (Eqs. 22-29, Gamma_i = 1 + s_i): the
+        //    column whose u, F, lap mu, grad phi this thread kept in step 4
         if (y >= ys) {
-            const int c = t;
+            constexpr int shift = strip_threads(SW) >= SW + 2 ? 1 : 0;
+            const int c = t - shift;
             const int gx = x0 + c;
-            if (gx < nx) {
+            if (c >= 0 && c < SW && gx < nx) {
                 const T *pc = atT(R.p[1]), *pu = atT(R.p[2]), *pd = atT(R.p[0]);
                 const bool lowghost = wall && y == 0;
                 const T pdm = lowghost ? T(2) * pc[c - 1] - pu[c - 1] : pd[c - 1];
@@ -677,7 +698,7 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
 // Single domain (or one y-slab of it, SLAB): CTA (bx, by) owns strip bx
 // and segment by of rows ya .. yb-1.
 template <class T, class ST, int SW, int DEPTH, bool SLAB>
-__global__ void __launch_bounds__(SW)
+__global__ void __launch_bounds__(strip_threads(SW))
 k_strip(const char *__restrict__ src, char *__restrict__ dst, const __grid_constant__ KP<T> P,
         int seg_h) {
     extern __shared__ __align__(16) char smem_raw[];
@@ -699,7 +720,7 @@ struct BatchDom {
 };
 
 template <class T, class ST, int SW, int DEPTH>
-__global__ void __launch_bounds__(SW)
+__global__ void __launch_bounds__(strip_threads(SW))
 k_strip_batch(char *__restrict__ state, const BatchDom<T> *__restrict__ doms,
               const BatchItem *__restrict__ items, int nitems, int parity) {
     extern __shared__ __align__(16) char smem_raw[];

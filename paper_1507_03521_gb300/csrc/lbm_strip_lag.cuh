@@ -46,7 +46,7 @@ struct LagSmem {
     static constexpr size_t pb = (size_t)LWP * sizeof(C);
     static constexpr size_t pop_bytes = gb * NBG + fb * NBF + pb * NBP;
     static constexpr size_t bytes = pop_bytes + sizeof(T) * ((size_t)RPHI * WPHI + (size_t)RMU * WMU);
-    static_assert(CHP <= SW, "one P chunk per thread");
+    static_assert(CHP <= strip_threads(SW), "one P chunk per thread");
 };
 
 // Ring slots (byte offsets into shared memory) of the rows live at
@@ -210,7 +210,7 @@ __device__ __forceinline__ void strip_body_lag(const char *__restrict__ src, cha
         if (y >= ys) {
             const int c = t;
             const int gx = x0 + c;
-            if (gx < nx) {
+            if (c < SW && gx < nx) {
                 const T *pu = atT(R.ph[2]), *pc = atT(R.ph[1]), *pd = atT(R.ph[0]);
                 const T *mu_ = atT(R.mu[2]), *mc = atT(R.mu[1]), *md = atT(R.mu[0]);
                 C f[9], g[9];
@@ -272,7 +272,7 @@ __device__ __forceinline__ void strip_body_lag(const char *__restrict__ src, cha
 }
 
 template <class T, class ST, int SW, int DEPTH>
-__global__ void __launch_bounds__(SW)
+__global__ void __launch_bounds__(strip_threads(SW))
 k_strip_lag(const char *__restrict__ src, char *__restrict__ dst, const __grid_constant__ KP<T> P,
             long long poff, int seg_h) {
     extern __shared__ __align__(16) char smem_raw[];
