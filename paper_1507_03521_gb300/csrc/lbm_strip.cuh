@@ -24,6 +24,8 @@
 //     extrapolated from the two rows inside (same rules as k_step).
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_internal.h"
 #include "lbm_kernels.cuh"
 
@@ -260,7 +262,13 @@ struct StripSmem {
     static constexpr int LW = SR::LW;
     // g rows are read 3 iterations after they arrive (phi, then collision),
     // f rows 1 iteration after (sum f and j, then collision): separate rings.
-    static constexpr int NBG = DEPTH + 4, NBF = DEPTH + 2;
+    // FP32 plain storage keeps each thread's own f values in registers from
+    // the moments (step 4) to the next iteration's collision, so its f ring
+    // holds only the row being summed and the rows in flight; F1 is the
+    // ring index of f row y+1.
+    static constexpr bool FCARRY = std::is_same<ST, PlainStore<float>>::value;
+    static constexpr int NBG = DEPTH + 4, NBF = FCARRY ? DEPTH + 1 : DEPTH + 2;
+    static constexpr int F1 = FCARRY ? 0 : 1;
     // rows live at iteration y: phi y..y+3, mu y..y+2, p y-1..y+1
     static constexpr int RPHI = 4, RMU = 3, RP = 3;
     static constexpr int WPHI = SW + 6, WMU = SW + 4, WQ = SW + 2;
@@ -272,6 +280,10 @@ struct StripSmem {
     static constexpr size_t bytes = pop_bytes + fld_elems * sizeof(T);
     // Order in shared memory: NBG g rows, NBF f rows, then the phi, mu and
     // p rings (RingSlots holds the offsets).
+    // CTAs per SM that the shared memory allows (228 KB per SM, 1 KB per CTA
+    // reserved): the register budget the compiler is held to, where the f
+    // carry makes it matter.
+    static constexpr int MINB = FCARRY ? int(233472 / (bytes + 1024)) : 1;
 };
 
 // The ring slots of the rows live at iteration y, as byte offsets into the
@@ -503,7 +515,7 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
         cp_async_commit();  // one group per iteration, possibly empty
     };
 #pragma unroll
-    for (int d = 0; d < DEPTH; ++d) issue_for(yfirst + d, R.g[d + 3], R.f[d + 1]);
+    for (int d = 0; d < DEPTH; ++d) issue_for(yfirst + d, R.g[d + 3], R.f[d + SM::F1]);
 
     // Interior strips never wrap in x when pushing; interior rows never wrap
     // or bounce in y.
@@ -513,6 +525,7 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     // iteration), n_* at row y+1 (computed in step 4 of this iteration)
     T c_ux = 0, c_uy = 0, c_Fx = 0, c_Fy = 0, c_lm = 0, c_gx = 0, c_gy = 0;
     T n_ux = 0, n_uy = 0, n_Fx = 0, n_Fy = 0, n_lm = 0, n_gx = 0, n_gy = 0;
+    T c_f[9] = {}, n_f[9] = {};  // own f values (FCARRY): row y, row y+1
 
     for (int y = yfirst; y < ye; ++y) {
         cp_async_wait<DEPTH - 1>();   // g row y+3, f row y+1 have landed (own chunks)
@@ -568,7 +581,7 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
             if (!wall || (r >= 0 && r < ny)) {
                 const T *pu = atT(R.ph[2]), *pc = atT(R.ph[1]), *pd = atT(R.ph[0]);
                 const T *mu_ = atT(R.mu[2]), *mc = atT(R.mu[1]), *md = atT(R.mu[0]);
-                const char *fbr = at(R.f[1]);
+                const char *fbr = at(R.f[SM::F1]);
                 auto point = [&](int c, bool keep) {
                     T f[9];
                     SR::read_f(fbr, c + HP, f);
@@ -604,6 +617,10 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
                         n_lm = lm;
                         n_gx = gphx;
                         n_gy = gphy;
+                        if constexpr (SM::FCARRY) {
+#pragma unroll
+                            for (int i = 0; i < 9; ++i) n_f[i] = f[i];
+                        }
                     }
                 };
                 if constexpr (strip_threads(SW) >= SW + 2) {
@@ -643,7 +660,12 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
                 const T pv = pc[c];
                 const T rho = P.rhoB + (phi - P.phiB) * P.drho;
                 T f[9], g[9];
-                SR::read_f(at(R.f[0]), c + HP, f);
+                if constexpr (SM::FCARRY) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) f[i] = c_f[i];
+                } else {
+                    SR::read_f(at(R.f[0]), c + HP, f);
+                }
                 SR::read_g(at(R.g[0]), c + HP, g);
                 T fv[9], gv[9];
                 collide(P, CellState<T>{phi, mu, pv, rho, c_ux, c_uy, c_Fx, c_Fy, c_lm, c_gx, c_gy,
@@ -690,6 +712,10 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
         c_lm = n_lm;
         c_gx = n_gx;
         c_gy = n_gy;
+        if constexpr (SM::FCARRY) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) c_f[i] = n_f[i];
+        }
         R.advance();
     }
     cp_async_wait<0>();
@@ -698,7 +724,7 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
 // Single domain (or one y-slab of it, SLAB): CTA (bx, by) owns strip bx
 // and segment by of rows ya .. yb-1.
 template <class T, class ST, int SW, int DEPTH, bool SLAB>
-__global__ void __launch_bounds__(strip_threads(SW))
+__global__ void __launch_bounds__(strip_threads(SW), (StripSmem<T, ST, SW, DEPTH>::MINB))
 k_strip(const char *__restrict__ src, char *__restrict__ dst, const __grid_constant__ KP<T> P,
         int seg_h) {
     extern __shared__ __align__(16) char smem_raw[];
@@ -720,7 +746,7 @@ struct BatchDom {
 };
 
 template <class T, class ST, int SW, int DEPTH>
-__global__ void __launch_bounds__(strip_threads(SW))
+__global__ void __launch_bounds__(strip_threads(SW), (StripSmem<T, ST, SW, DEPTH>::MINB))
 k_strip_batch(char *__restrict__ state, const BatchDom<T> *__restrict__ doms,
               const BatchItem *__restrict__ items, int nitems, int parity) {
     extern __shared__ __align__(16) char smem_raw[];
