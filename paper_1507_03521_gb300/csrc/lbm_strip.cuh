@@ -262,11 +262,14 @@ struct StripSmem {
     static constexpr int LW = SR::LW;
     // g rows are read 3 iterations after they arrive (phi, then collision),
     // f rows 1 iteration after (sum f and j, then collision): separate rings.
-    // FP32 plain storage keeps each thread's own f values in registers from
-    // the moments (step 4) to the next iteration's collision, so its f ring
-    // holds only the row being summed and the rows in flight; F1 is the
-    // ring index of f row y+1.
-    static constexpr bool FCARRY = std::is_same<ST, PlainStore<float>>::value;
+    // FP32 plain storage on one-pass strips keeps each thread's own f values
+    // in registers from the moments (step 4) to the next iteration's
+    // collision, so its f ring holds only the row being summed and the rows
+    // in flight (one row less: 6 CTAs per SM instead of 5); F1 is the ring
+    // index of f row y+1.  At 128-column strips the carry frees no CTA slot
+    // and only adds moves, so it is off there.
+    static constexpr bool FCARRY =
+        std::is_same<ST, PlainStore<float>>::value && strip_threads(SW) != SW;
     static constexpr int NBG = DEPTH + 4, NBF = FCARRY ? DEPTH + 1 : DEPTH + 2;
     static constexpr int F1 = FCARRY ? 0 : 1;
     // rows live at iteration y: phi y..y+3, mu y..y+2, p y-1..y+1
@@ -280,10 +283,11 @@ struct StripSmem {
     static constexpr size_t bytes = pop_bytes + fld_elems * sizeof(T);
     // Order in shared memory: NBG g rows, NBF f rows, then the phi, mu and
     // p rings (RingSlots holds the offsets).
-    // CTAs per SM that the shared memory allows (228 KB per SM, 1 KB per CTA
-    // reserved): the register budget the compiler is held to, where the f
-    // carry makes it matter.
-    static constexpr int MINB = FCARRY ? int(233472 / (bytes + 1024)) : 1;
+    // With the f carry, the CTAs per SM that the shared memory allows (228
+    // KB per SM, 1 KB per CTA reserved) become the register budget the
+    // compiler is held to, so that registers do not become the tighter
+    // limit; otherwise (0) the compiler's own choice stands.
+    static constexpr int MINB = FCARRY ? int(233472 / (bytes + 1024)) : 0;
 };
 
 // The ring slots of the rows live at iteration y, as byte offsets into the
@@ -507,11 +511,13 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     auto atT = [&](int off) { return reinterpret_cast<T *>(smem_raw + off); };
 
     // Iteration y reads g row y+3 and f row y+1 first; both are issued
-    // DEPTH iterations earlier, as one commit group.
+    // DEPTH iterations earlier, as one commit group.  The collisions of the
+    // segment need p from row ys-1 on, so the f rows of the first warm-up
+    // iterations are not loaded (the p they would give is never used).
     auto issue_for = [&](int it, int gslot, int fslot) {
         const int gr = it + 3, fr = it + 1;
         if (gr <= ye + 2) SR::issue_g(desc, at(gslot), src, buf_row<SLAB>(P, gr) * nx);
-        if (fr <= ye) SR::issue_f(desc, at(fslot), src, buf_row<SLAB>(P, fr) * nx);
+        if (fr >= ys - 1 && fr <= ye) SR::issue_f(desc, at(fslot), src, buf_row<SLAB>(P, fr) * nx);
         cp_async_commit();  // one group per iteration, possibly empty
     };
 #pragma unroll
