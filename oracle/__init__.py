@@ -22,6 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "orc.c")
+_SRC3 = os.path.join(_HERE, "orc3.c")  # the D3Q19 statement, same library
 _LIB = os.path.join(_HERE, "liborc.so")
 
 PERIODIC = 0
@@ -31,11 +32,11 @@ WALL = 1
 def build(force: bool = False) -> str:
     """Compile ``orc.c`` into ``liborc.so`` (plain gcc, no FMA contraction)."""
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC3))):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
-           "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+           "-fPIC", "-shared", _SRC, _SRC3, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -48,11 +49,11 @@ def build_omp(force: bool = False) -> str:
     """The same source built with OpenMP (``liborc_omp.so``): the passes
     over cells run on all host cores, bit-identical to ``liborc.so``."""
     if (not force and os.path.exists(_LIB_OMP)
-            and os.path.getmtime(_LIB_OMP) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB_OMP) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC3))):
         return _LIB_OMP
     tmp = _LIB_OMP + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fopenmp",
-           "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+           "-fPIC", "-shared", _SRC, _SRC3, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_OMP)
     return _LIB_OMP
@@ -84,7 +85,7 @@ def build_mutant(k: int, outdir: str) -> str:
     """Build the oracle with mistake number k planted (mutation tests only)."""
     out = os.path.join(outdir, f"liborc_mutant{k}.so")
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC",
-           "-shared", f"-DORC_MUTANT={k}", _SRC, "-o", out, "-lm"]
+           "-shared", f"-DORC_MUTANT={k}", _SRC, _SRC3, "-o", out, "-lm"]
     subprocess.run(cmd, check=True)
     return out
 
@@ -117,6 +118,19 @@ def _load(path: str | None = None):
     lib.orc_stencils.argtypes = [ctypes.c_int] * 4 + [_dp] * 4
     lib.orc_lattice.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dp]
     lib.orc_set_gradp_lag.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.orc3_create.restype = ctypes.c_void_p
+    lib.orc3_create.argtypes = [ctypes.POINTER(_Params), ctypes.c_int]
+    lib.orc3_destroy.argtypes = [ctypes.c_void_p]
+    lib.orc3_init_phi.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
+    lib.orc3_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
+    lib.orc3_fields.argtypes = [ctypes.c_void_p] + [_dp] * 7
+    lib.orc3_mass.argtypes = [ctypes.c_void_p, _dp, _dp]
+    lib.orc3_laplace.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 4 + [_dp, _dp]
+    lib.orc3_get_pops.argtypes = [ctypes.c_void_p, _dp, _dp]
+    lib.orc3_step_count.restype = ctypes.c_long
+    lib.orc3_step_count.argtypes = [ctypes.c_void_p]
+    lib.orc3_stencils.argtypes = [ctypes.c_int] * 3 + [_dp] * 5
+    lib.orc3_lattice.argtypes = [ctypes.POINTER(ctypes.c_int)] * 3 + [_dp]
     lib.orc_set_threads.restype = ctypes.c_int
     lib.orc_set_threads.argtypes = [ctypes.c_int]
     _libs[path] = lib
@@ -271,3 +285,85 @@ def lattice():
     w = np.zeros(9)
     lib.orc_lattice(cx, cy, _ptr(w))
     return np.array(list(cx)), np.array(list(cy)), w
+
+
+class Oracle3:
+    """One FP64 periodic domain of the D3Q19 statement (orc3.c); fields are
+    [nz, ny, nx] arrays, populations [19, nz, ny, nx]."""
+
+    def __init__(self, p: Params | dict, nz: int, lib: str | None = None):
+        if isinstance(p, dict):
+            p = params_from_dict(p)
+        self.p = p
+        self._lib = _load(lib)
+        self._cp = p._c()
+        h = self._lib.orc3_create(ctypes.byref(self._cp), int(nz))
+        if not h:
+            raise ValueError(f"oracle rejected parameters {p} nz={nz}")
+        self._h = ctypes.c_void_p(h)
+        self.shape = (int(nz), p.ny, p.nx)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.orc3_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _arr(self, a):
+        return None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(self.shape)
+
+    def init_phi(self, phi0, ux0=None, uy0=None, uz0=None):
+        arrs = [self._arr(a) for a in (phi0, ux0, uy0, uz0)]
+        self._keep = arrs
+        self._lib.orc3_init_phi(self._h, *[_ptr(a) for a in arrs])
+
+    def step(self, n: int = 1):
+        self._lib.orc3_step(self._h, int(n))
+
+    @property
+    def step_count(self) -> int:
+        return self._lib.orc3_step_count(self._h)
+
+    def fields(self) -> dict:
+        keys = ("phi", "rho", "p", "ux", "uy", "uz", "mu")
+        out = {k: np.zeros(self.shape) for k in keys}
+        self._lib.orc3_fields(self._h, *[_ptr(out[k]) for k in keys])
+        return out
+
+    def mass(self):
+        m, t = ctypes.c_double(), ctypes.c_double()
+        self._lib.orc3_mass(self._h, ctypes.byref(m), ctypes.byref(t))
+        return m.value, t.value
+
+    def laplace(self, xc, yc, zc, R):
+        dP, Re = ctypes.c_double(), ctypes.c_double()
+        self._lib.orc3_laplace(self._h, float(xc), float(yc), float(zc), float(R), ctypes.byref(dP),
+                               ctypes.byref(Re))
+        return dP.value, Re.value
+
+    def pops(self):
+        f = np.zeros((19,) + self.shape)
+        g = np.zeros((19,) + self.shape)
+        self._lib.orc3_get_pops(self._h, _ptr(f), _ptr(g))
+        return f, g
+
+
+def stencils3(chi):
+    """Isotropic D3Q19 gradient and Laplacian of a periodic [nz, ny, nx] field."""
+    chi = np.ascontiguousarray(chi, dtype=np.float64)
+    nz, ny, nx = chi.shape
+    out = [np.zeros_like(chi) for _ in range(4)]
+    _load().orc3_stencils(nx, ny, nz, _ptr(chi), *[_ptr(o) for o in out])
+    return out
+
+
+def lattice3():
+    cx, cy, cz = [(ctypes.c_int * 19)() for _ in range(3)]
+    w = np.zeros(19)
+    _load().orc3_lattice(cx, cy, cz, _ptr(w))
+    return np.array(cx[:]), np.array(cy[:]), np.array(cz[:]), w
