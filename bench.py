@@ -345,6 +345,39 @@ def measure_lagged(lbm, p, phi, args, peak, mlups_sync, dist):
             "max_abs_diff_vs_synchronous": diff, "steps_for_diff": args.steps + args.warmup}
 
 
+def measure_3d(lbm, W, args, peak, dist):
+    """The D3Q19 step on the 3-D analogue of the precision workload: 256^3
+    periodic, 64 spherical droplets, rho ratio 100, FP32; four launches per
+    step.  Algorithmic bytes: 19 + 19 FP32 populations read and written,
+    304 B per cell."""
+    import torch
+    p, phi, nz = W.precision3d()
+    sim = lbm.Sim3(p, nz, "f32")
+    sim.init_phi(phi)
+    sim.step(args.warmup)
+    st = sim.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0.record(st)
+    sim.step(args.steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    world = dist.get_world_size() if dist is not None else 1
+    cells = p["nx"] * p["ny"] * nz
+    mlups = cells * args.steps * world / (ms * 1e-3) / 1e6
+    gbs = 304 * cells / (ms / args.steps * 1e-3) / 1e9
+    m0 = sim.mass()
+    sim.close()
+    return {"workload": "precision3d-256^3-64-droplets-rho100", "dtype": "f32",
+            "mlups": round(mlups, 2), "ms_per_step": round(ms / args.steps, 5),
+            "bytes_per_cell": 304, "hbm_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+            "launches_per_step": 4, "traffic_per_step": _traffic("d3q19_f32"),
+            "finite": bool(np.isfinite(m0[0]))}
+
+
 def measure_adjoint(W):
     """Adjoint workload: droplet in shear, 512 x 512, R = 64, walls at
     +-0.01, rho ratio 10, FP32, 4000 steps, checkpoints every 200 steps;
@@ -394,6 +427,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint workload")
     ap.add_argument("--no-slabs", action="store_true", help="skip the y-slab decomposition")
     ap.add_argument("--no-lagged", action="store_true", help="skip the lagged-grad-p variant")
+    ap.add_argument("--no-3d", action="store_true", help="skip the D3Q19 workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -505,6 +539,8 @@ def main():
         line["slabs"] = measure_slabs(lbm, p, phi, args, mlups, dist)
     if not args.no_lagged:
         line["gradp_lag"] = measure_lagged(lbm, p, phi, args, peak, mlups, dist)
+    if not args.no_3d:
+        line["d3q19"] = measure_3d(lbm, W, args, peak, dist)
     if not args.no_adjoint:
         line["adjoint"] = measure_adjoint(W)
 

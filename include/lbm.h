@@ -303,6 +303,49 @@ LBM_API int64_t lbm_slabs_step_count(const lbm_slabs *s);
 LBM_API const char *lbm_slabs_last_error(const lbm_slabs *s);
 LBM_API void lbm_slabs_destroy(lbm_slabs *s);
 
+/* ------------------------------------------------------------------ 3-D
+ * The same step on D3Q19 (Sec. 3 says the scheme carries over to other
+ * lattices; the paper works in 2-D): every formula of Eqs. 22-32 with
+ * three-component vectors, weights 1/3 (rest), 1/18 (6 axis directions),
+ * 1/36 (12 edge diagonals), c_s^2 = 1/3, the isotropic stencils built from
+ * those weights, body force F_b = (0, -(rho - rho_ref) gravity, 0).
+ * Periodic in x, y and z; LBM_F32 or LBM_F64; nx * ny * nz < 2^31.
+ * prm->bc_y must be LBM_PERIODIC and prm->gradp_lag 0.  Fields are
+ * [nz][ny][nx], x fastest, in the field type, on the device.  A step is
+ * four launches: phi, mu, p (each into the work buffer), then the
+ * collision and push into the other level (populations f_0..18, g_0..18,
+ * 2 x 152 B per cell in FP32).
+ */
+typedef struct lbm3_sim lbm3_sim; /* opaque handle, owned by the caller */
+
+/* Device bytes of the two population levels and of the work buffer
+ * (phi, mu, p fields and reduction partials).  Errors: LBM_ERR_ARG. */
+LBM_API lbm_status lbm3_buffer_sizes(const lbm_params *prm, int nz, size_t *state_bytes,
+                                     size_t *work_bytes);
+LBM_API lbm_status lbm3_create(const lbm_params *prm, int nz, void *stream, lbm3_sim **out);
+/* Caller-owned, 256-byte aligned device buffers. */
+LBM_API lbm_status lbm3_bind_buffers(lbm3_sim *s, void *state, size_t state_bytes, void *work,
+                                     size_t work_bytes);
+/* Equilibrium initial state from phi (p = 0, u = (ux, uy, uz), NULL = 0);
+ * device pointers of the field type. */
+LBM_API lbm_status lbm3_init_phi(lbm3_sim *s, const void *phi, const void *ux, const void *uy,
+                                 const void *uz);
+/* Advance n >= 0 steps (asynchronous). */
+LBM_API lbm_status lbm3_step(lbm3_sim *s, int64_t n);
+/* phi, rho, p, u, mu of the current level (device pointers or NULL). */
+LBM_API lbm_status lbm3_fields(lbm3_sim *s, void *phi, void *rho, void *p, void *ux, void *uy,
+                               void *uz, void *mu);
+/* sum rho and sum phi in FP64, fixed order; synchronises the stream. */
+LBM_API lbm_status lbm3_mass(lbm3_sim *s, double *mass, double *phi_total);
+/* Laplace diagnostic of a droplet centred at (xc, yc, zc), nominal radius R:
+ * total pressure of Sec. 4.2 averaged over r < R - 2W minus over
+ * r > R + 2W; R_eff = (3 V / 4 pi)^(1/3) from the volume of fluid A. */
+LBM_API lbm_status lbm3_laplace(lbm3_sim *s, double xc, double yc, double zc, double R,
+                                double *dP, double *R_eff);
+LBM_API int64_t lbm3_step_count(const lbm3_sim *s);
+LBM_API const char *lbm3_last_error(const lbm3_sim *s);
+LBM_API void lbm3_destroy(lbm3_sim *s);
+
 /* The mass diagnostic of lbm_mass for callers that cannot allocate device
  * memory.  The paper has no counterpart: this is a library convenience.
  *

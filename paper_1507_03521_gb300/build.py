@@ -29,6 +29,7 @@ UNITS = {
     "lbm_noalloc": [],
     "lbm_batch": [],
     "lbm_slabs": [],
+    "lbm3": [],
 }
 
 

@@ -36,7 +36,10 @@ EXPORTS = ["lbm_version", "lbm_buffer_sizes", "lbm_create", "lbm_bind_buffers", 
            "lbm_adj_step", "lbm_adj_init", "lbm_adj_grads",
            "lbm_slabs_buffer_sizes", "lbm_slabs_create", "lbm_slabs_bind_buffers",
            "lbm_slabs_scatter", "lbm_slabs_gather", "lbm_slabs_step", "lbm_slabs_rows",
-           "lbm_slabs_step_count", "lbm_slabs_last_error", "lbm_slabs_destroy"]
+           "lbm_slabs_step_count", "lbm_slabs_last_error", "lbm_slabs_destroy",
+           "lbm3_buffer_sizes", "lbm3_create", "lbm3_bind_buffers", "lbm3_init_phi", "lbm3_step",
+           "lbm3_fields", "lbm3_mass", "lbm3_laplace", "lbm3_step_count", "lbm3_last_error",
+           "lbm3_destroy"]
 
 
 class LBMError(RuntimeError):
@@ -163,6 +166,29 @@ def load(path: str = LIB_PATH):
     lib.lbm_slabs_last_error.argtypes = [_vp]
     lib.lbm_slabs_destroy.restype = None
     lib.lbm_slabs_destroy.argtypes = [_vp]
+    lib.lbm3_buffer_sizes.restype = S
+    lib.lbm3_buffer_sizes.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t),
+                                      ctypes.POINTER(ctypes.c_size_t)]
+    lib.lbm3_create.restype = S
+    lib.lbm3_create.argtypes = [P, ctypes.c_int, _vp, ctypes.POINTER(_vp)]
+    lib.lbm3_bind_buffers.restype = S
+    lib.lbm3_bind_buffers.argtypes = [_vp, _vp, ctypes.c_size_t, _vp, ctypes.c_size_t]
+    lib.lbm3_init_phi.restype = S
+    lib.lbm3_init_phi.argtypes = [_vp, _vp, _vp, _vp, _vp]
+    lib.lbm3_step.restype = S
+    lib.lbm3_step.argtypes = [_vp, ctypes.c_int64]
+    lib.lbm3_fields.restype = S
+    lib.lbm3_fields.argtypes = [_vp] + [_vp] * 7
+    lib.lbm3_mass.restype = S
+    lib.lbm3_mass.argtypes = [_vp, _dp, _dp]
+    lib.lbm3_laplace.restype = S
+    lib.lbm3_laplace.argtypes = [_vp] + [ctypes.c_double] * 4 + [_dp, _dp]
+    lib.lbm3_step_count.restype = ctypes.c_int64
+    lib.lbm3_step_count.argtypes = [_vp]
+    lib.lbm3_last_error.restype = ctypes.c_char_p
+    lib.lbm3_last_error.argtypes = [_vp]
+    lib.lbm3_destroy.restype = None
+    lib.lbm3_destroy.argtypes = [_vp]
     lib.lbm_adj_work_bytes.restype = S
     lib.lbm_adj_work_bytes.argtypes = [_vp, ctypes.POINTER(ctypes.c_size_t)]
     lib.lbm_adj_reset.restype = S
@@ -441,6 +467,96 @@ class Slabs:
 
     def step(self, n=1):
         self._check(self._lib.lbm_slabs_step(self._h, int(n)))
+
+
+class Sim3:
+    """One periodic D3Q19 domain (lbm3_*): fields are [nz, ny, nx] tensors of
+    the field type; ``dtype`` "f32" or "f64"."""
+
+    def __init__(self, params: dict, nz: int, dtype="f32", stream=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblbm needs a CUDA device; none is available")
+        self._lib = load()
+        self.params = dict(params)
+        self.nz = int(nz)
+        self.dtype = dtype
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.field_dtype = torch.float64 if dtype == "f64" else torch.float32
+        self.shape = (self.nz, params["ny"], params["nx"])
+        self._cp = make_params(self.params, dtype)
+        sb, wb = ctypes.c_size_t(), ctypes.c_size_t()
+        st = self._lib.lbm3_buffer_sizes(ctypes.byref(self._cp), self.nz, ctypes.byref(sb),
+                                         ctypes.byref(wb))
+        if st != 0:
+            raise LBMError(st, self._lib.lbm_create_error().decode())
+        h = _vp()
+        st = self._lib.lbm3_create(ctypes.byref(self._cp), self.nz, _vp(self.stream.cuda_stream),
+                                   ctypes.byref(h))
+        if st != 0:
+            raise LBMError(st, self._lib.lbm_create_error().decode())
+        self._h = h
+        self.state_buf = torch.empty(sb.value, dtype=torch.uint8, device=self.device)
+        self.work_buf = torch.empty(wb.value, dtype=torch.uint8, device=self.device)
+        self._check(self._lib.lbm3_bind_buffers(h, self.state_buf.data_ptr(), sb.value,
+                                                self.work_buf.data_ptr(), wb.value))
+
+    def _check(self, st):
+        if st != 0:
+            raise LBMError(st, self._lib.lbm3_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.stream.synchronize()
+            self._lib.lbm3_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _t(self, a):
+        import torch
+        if a is None:
+            return None
+        if isinstance(a, np.ndarray):
+            a = torch.from_numpy(np.ascontiguousarray(a))
+        return a.to(device=self.device, dtype=self.field_dtype).contiguous().reshape(self.shape)
+
+    def init_phi(self, phi, ux=None, uy=None, uz=None):
+        t = [self._t(a) for a in (phi, ux, uy, uz)]
+        self._keep = t
+        self._check(self._lib.lbm3_init_phi(self._h, *[None if a is None else a.data_ptr() for a in t]))
+
+    def step(self, n: int = 1):
+        self._check(self._lib.lbm3_step(self._h, int(n)))
+
+    @property
+    def step_count(self) -> int:
+        return self._lib.lbm3_step_count(self._h)
+
+    def fields(self, names=("phi", "rho", "p", "ux", "uy", "uz", "mu")):
+        import torch
+        out = {k: torch.empty(self.shape, dtype=self.field_dtype, device=self.device) for k in names}
+        ptr = [out[k].data_ptr() if k in out else None
+               for k in ("phi", "rho", "p", "ux", "uy", "uz", "mu")]
+        self._check(self._lib.lbm3_fields(self._h, *ptr))
+        self.stream.synchronize()
+        return out
+
+    def mass(self):
+        m, t = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.lbm3_mass(self._h, ctypes.byref(m), ctypes.byref(t)))
+        return m.value, t.value
+
+    def laplace(self, xc, yc, zc, R):
+        dP, Re = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.lbm3_laplace(self._h, float(xc), float(yc), float(zc), float(R),
+                                           ctypes.byref(dP), ctypes.byref(Re)))
+        return dP.value, Re.value
 
 
 class Batch:

@@ -166,6 +166,60 @@ def paper_flat(nx=10, ny=100, Pe=50.0, Cn=4.0):
     return p, phi
 
 
+def droplet3_field(nx, ny, nz, centres, radii, W, phi_A, phi_B):
+    """phi of spherical droplets (maximum over droplets of the tanh profile,
+    nearest periodic image), background phi_B; array [nz, ny, nx].  Each
+    droplet is evaluated on its periodic bounding box of radius R + 10W;
+    beyond it tanh(2(R - r)/W) rounds to -1 in double precision, so the
+    field equals the direct evaluation."""
+    mid, half = 0.5 * (phi_A + phi_B), 0.5 * (phi_A - phi_B)
+    out = np.full((nz, ny, nx), float(phi_B))
+    for (cx, cy, cz), R in zip(centres, radii):
+        reach = R + 10.0 * W
+        axes = []
+        for c, n in ((cz, nz), (cy, ny), (cx, nx)):
+            lo, hi = int(np.floor(c - reach)), int(np.ceil(c + reach))
+            idx = np.arange(lo, hi + 1) if hi - lo + 1 < n else np.arange(n)
+            d = np.abs(idx.astype(np.float64) - c)
+            if hi - lo + 1 >= n:
+                d = np.minimum(d, n - d)
+            axes.append((np.mod(idx, n), d))
+        (iz, dz), (iy, dy), (ix, dx) = axes
+        r = np.sqrt(dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2)
+        box = mid + half * np.tanh(2.0 * (R - r) / W)
+        sub = out[np.ix_(iz, iy, ix)]
+        out[np.ix_(iz, iy, ix)] = np.maximum(sub, box)
+    return out
+
+
+def precision3d(n=256, n_drops=64, seed=1507037):
+    """The precision workload's 3-D analogue: n^3 periodic, n_drops spherical
+    droplets of fluid A (phi = 1), radii U[6, 16], centres uniform and
+    rejection-sampled at least R1 + R2 + 2W apart (PCG64 seed), background
+    phi = -1; W = 4, rho_A = 1, rho_B = 0.01, sigma = 1e-3, M = 0.05,
+    tau = 0.8.  Returns (params, phi [nz, ny, nx], nz)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Wd = 4.0
+    centres, radii = [], []
+    tries = 0
+    while len(centres) < n_drops and tries < 200000:
+        tries += 1
+        R = rng.uniform(6.0, 16.0)
+        c = rng.uniform(0, n, size=3)
+        ok = True
+        for c2, R2 in zip(centres, radii):
+            d = np.abs(c - c2)
+            d = np.minimum(d, n - d)
+            if np.sqrt((d * d).sum()) < R + R2 + 2 * Wd:
+                ok = False
+                break
+        if ok:
+            centres.append(c)
+            radii.append(R)
+    p = _base(nx=n, ny=n, rho_A=1.0, rho_B=0.01, sigma=1e-3, M=0.05)
+    return p, droplet3_field(n, n, n, centres, radii, Wd, 1.0, -1.0), n
+
+
 def paper_bubble(nx=160, ny=480, R=32.0, yc=120.0, Pe=50.0, Cn=4.0):
     """Bubble rising under buoyancy, Sec. 4.3: 160 x 480 periodic, a light
     bubble of fluid B (phi_B = 0, rho_B = 0.5) of radius 32 in fluid A

@@ -21,7 +21,7 @@ def lib():
 
 def _declared():
     txt = open(HEADER).read()
-    return set(re.findall(r"LBM_API[^;(]*?\b(lbm_\w+)\s*\(", txt))
+    return set(re.findall(r"LBM_API[^;(]*?\b(lbm3?_\w+)\s*\(", txt))
 
 
 def test_exports_match_header(lib):
