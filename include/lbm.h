@@ -309,7 +309,8 @@ LBM_API void lbm_slabs_destroy(lbm_slabs *s);
  * three-component vectors, weights 1/3 (rest), 1/18 (6 axis directions),
  * 1/36 (12 edge diagonals), c_s^2 = 1/3, the isotropic stencils built from
  * those weights, body force F_b = (0, -(rho - rho_ref) gravity, 0).
- * Periodic in x, y and z; LBM_F32 or LBM_F64; nx * ny * nz < 2^31.
+ * Periodic in x, y and z; LBM_F32 or LBM_F64; nx * ny * nz < 2^31 and
+ * ny, nz <= 65535.
  * prm->bc_y must be LBM_PERIODIC and prm->gradp_lag 0.  Fields are
  * [nz][ny][nx], x fastest, in the field type, on the device.  A step is
  * four launches: phi, mu, p (each into the work buffer), then the

@@ -46,6 +46,7 @@ std::string check3(const lbm_params *p, int nz) {
     if (p->dtype != LBM_F32 && p->dtype != LBM_F64) return "the 3-D step supports LBM_F32 and LBM_F64";
     if (p->gradp_lag) return "the 3-D step is the synchronous scheme (gradp_lag = 0)";
     if ((long long)p->nx * p->ny * nz >= (1LL << 31)) return "grid too large for the 3-D step";
+    if (p->ny > 65535 || nz > 65535) return "ny and nz must be <= 65535 for the 3-D step";
     return "";
 }
 
@@ -94,6 +95,9 @@ struct lbm3_sim {
     double *part() const { return reinterpret_cast<double *>(work + L.part_off); }
     double *out() const { return reinterpret_cast<double *>(work + L.out_off); }
     unsigned blocks() const { return (unsigned)((L.N + kThreads - 1) / kThreads); }
+    // step kernels: one row of x per block column, y and z from the grid
+    unsigned row_threads() const { return d.nx >= 128 ? 128u : (unsigned)((d.nx + 31) / 32 * 32); }
+    dim3 rows() const { return dim3((unsigned)((d.nx + row_threads() - 1) / row_threads()), (unsigned)d.ny, (unsigned)nz); }
     lbm_status fail(lbm_status s, const std::string &m) {
         err = m;
         return s;
@@ -111,13 +115,13 @@ struct lbm3_sim {
     template <class T>
     void phi_mu(const K3<T> &P) {
         const T *lvl = reinterpret_cast<const T *>(level(cur));
-        lbm3::k3_phi<T><<<blocks(), kThreads, 0, stream>>>(lvl, reinterpret_cast<T *>(field(0)), P);
-        lbm3::k3_mu<T><<<blocks(), kThreads, 0, stream>>>(reinterpret_cast<const T *>(field(0)),
+        lbm3::k3_phi<T><<<rows(), row_threads(), 0, stream>>>(lvl, reinterpret_cast<T *>(field(0)), P);
+        lbm3::k3_mu<T><<<rows(), row_threads(), 0, stream>>>(reinterpret_cast<const T *>(field(0)),
                                                            reinterpret_cast<T *>(field(1)), P);
     }
     template <class T>
     void pressure(const K3<T> &P) {
-        lbm3::k3_p<T><<<blocks(), kThreads, 0, stream>>>(
+        lbm3::k3_p<T><<<rows(), row_threads(), 0, stream>>>(
             reinterpret_cast<const T *>(level(cur)), reinterpret_cast<const T *>(field(0)),
             reinterpret_cast<const T *>(field(1)), reinterpret_cast<T *>(field(2)), P);
     }
@@ -127,7 +131,7 @@ struct lbm3_sim {
         for (int64_t t = 0; t < n; ++t) {
             phi_mu(P);
             pressure(P);
-            lbm3::k3_collide<T><<<blocks(), kThreads, 0, stream>>>(
+            lbm3::k3_collide<T><<<rows(), row_threads(), 0, stream>>>(
                 reinterpret_cast<const T *>(level(cur)), reinterpret_cast<T *>(level(1 - cur)),
                 reinterpret_cast<const T *>(field(0)), reinterpret_cast<const T *>(field(1)),
                 reinterpret_cast<const T *>(field(2)), P);
@@ -140,7 +144,7 @@ struct lbm3_sim {
     template <class T>
     lbm_status init_t(const void *phi, const void *ux, const void *uy, const void *uz) {
         const K3<T> P = make_k3<T>(d, nz, L);
-        lbm3::k3_mu<T><<<blocks(), kThreads, 0, stream>>>(static_cast<const T *>(phi),
+        lbm3::k3_mu<T><<<rows(), row_threads(), 0, stream>>>(static_cast<const T *>(phi),
                                                            reinterpret_cast<T *>(field(1)), P);
         lbm3::k3_init<T><<<blocks(), kThreads, 0, stream>>>(
             static_cast<const T *>(phi), reinterpret_cast<const T *>(field(1)),

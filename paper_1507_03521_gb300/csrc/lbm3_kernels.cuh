@@ -56,23 +56,36 @@ struct K3 {
 };
 
 // Neighbour cells of a cell (periodic in x, y, z); grids stay below 2^31
-// cells, so 32-bit indices.
+// cells, so 32-bit indices.  Each offset is k plus an x, a y and a z step,
+// the steps taking the periodic wrap at the faces.
 struct Nbr3 {
     int k;
     int o[19];
-    __device__ __forceinline__ Nbr3(int kk, int nx, int ny, int nz) : k(kk) {
-        const int x = kk % nx;
+    __device__ __forceinline__ Nbr3(int x, int y, int z, int nx, int ny, int nz) { set(x, y, z, nx, ny, nz); }
+    __device__ __forceinline__ Nbr3(int kk, int nx, int ny, int nz) {
         const int r = kk / nx;
-        const int y = r % ny;
-        const int z = r / ny;
-        const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
-        const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
-        const int zs[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
+        set(kk - r * nx, r % ny, r / ny, nx, ny, nz);
+    }
+    __device__ __forceinline__ void set(int x, int y, int z, int nx, int ny, int nz) {
+        const int np = nx * ny;
+        k = (z * ny + y) * nx + x;
+        const int dx[3] = {x == 0 ? nx - 1 : -1, 0, x == nx - 1 ? 1 - nx : 1};
+        const int dy[3] = {y == 0 ? np - nx : -nx, 0, y == ny - 1 ? nx - np : nx};
+        const int dz[3] = {z == 0 ? (nz - 1) * np : -np, 0, z == nz - 1 ? (1 - nz) * np : np};
 #pragma unroll
-        for (int i = 0; i < 19; ++i)
-            o[i] = (zs[1 + D3Q19::cz(i)] * ny + ys[1 + D3Q19::cy(i)]) * nx + xs[1 + D3Q19::cx(i)];
+        for (int i = 0; i < 19; ++i) o[i] = k + dz[1 + D3Q19::cz(i)] + dy[1 + D3Q19::cy(i)] + dx[1 + D3Q19::cx(i)];
     }
 };
+
+// Cell of this thread in the step kernels' launch: x along the block's
+// threads, y = blockIdx.y, z = blockIdx.z; false past the x extent.
+template <class T>
+__device__ __forceinline__ bool cell3(const K3<T> &P, int &x, int &y, int &z) {
+    x = blockIdx.x * blockDim.x + threadIdx.x;
+    y = blockIdx.y;
+    z = blockIdx.z;
+    return x < P.nx;
+}
 
 template <class T>
 __device__ __forceinline__ void grad3(const T *__restrict__ a, const Nbr3 &n, T g[3]) {
@@ -148,8 +161,9 @@ __device__ __forceinline__ Macro3<T> macro3(const K3<T> &P, const T f[19], const
 
 template <class T>
 __global__ void k3_phi(const T *__restrict__ lvl, T *__restrict__ phi, const K3<T> P) {
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= P.N) return;
+    int x, y, z;
+    if (!cell3(P, x, y, z)) return;
+    const int k = (z * P.ny + y) * P.nx + x;
     const T *g = lvl + 19 * P.NS + k;
     T s = 0;
 #pragma unroll
@@ -159,33 +173,61 @@ __global__ void k3_phi(const T *__restrict__ lvl, T *__restrict__ phi, const K3<
 
 template <class T>
 __global__ void k3_mu(const T *__restrict__ phi, T *__restrict__ mu, const K3<T> P) {
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= P.N) return;
-    const Nbr3 n((int)k, P.nx, P.ny, P.nz);
-    mu[k] = mu_of(P, __ldg(phi + k), lap3(phi, n));
+    int x, y, z;
+    if (!cell3(P, x, y, z)) return;
+    const Nbr3 n(x, y, z, P.nx, P.ny, P.nz);
+    mu[n.k] = mu_of(P, __ldg(phi + n.k), lap3(phi, n));
 }
 
 template <class T>
 __global__ void k3_p(const T *__restrict__ lvl, const T *__restrict__ phi, const T *__restrict__ mu,
                      T *__restrict__ p, const K3<T> P) {
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= P.N) return;
-    const Nbr3 n((int)k, P.nx, P.ny, P.nz);
+    int x, y, z;
+    if (!cell3(P, x, y, z)) return;
+    const Nbr3 n(x, y, z, P.nx, P.ny, P.nz);
+    const int k = n.k;
     T f[19];
 #pragma unroll
     for (int i = 0; i < 19; ++i) f[i] = __ldg(lvl + i * P.NS + k);
     p[k] = macro3(P, f, phi, mu, n).p;
 }
 
+__device__ __forceinline__ float2 bc3(float a) { return make_float2(a, a); }
+
+// One opposite pair of directions (c, -c) in the two lanes: the
+// projections on c (cu = c.u, cF = c.F, cZ = c.F + c.grad(rho)/3,
+// cD = c.(grad p - F)) change sign in the second lane; the mu* terms are
+// minus the matching u projections.  s = cu (3 + 4.5 cu) - 1.5 u.u (Eq. 26)
+// and the f, g collisions of Eqs. 22-29 with Gamma = 1 + s.
+__device__ __forceinline__ void collide_pair3(float2 cu, float2 cF, float2 cZ, float2 cD, float w,
+                                              float2 mu15, float2 muF, float2 muZ, float2 muD,
+                                              float2 Kf, float2 Bf, float2 pf, float2 omf, float2 Ag,
+                                              float2 phg, float2 Q, float2 omg, float2 f, float2 g,
+                                              float2 &fo, float2 &go) {
+    const float2 sg = make_float2(1.0f, -1.0f);
+    const float2 si = __ffma2_rn(cu, __ffma2_rn(cu, bc3(4.5f), make_float2(3.0f, -3.0f)), mu15);
+    const float2 eF = __ffma2_rn(cF, sg, muF);
+    const float2 eZ = __ffma2_rn(cZ, sg, muZ);
+    const float2 eD = __ffma2_rn(cD, sg, muD);
+    const float2 w2 = bc3(w);
+    float2 a = __ffma2_rn(Bf, si, Kf);
+    a = __ffma2_rn(pf, __ffma2_rn(si, eZ, eF), a);
+    fo = __ffma2_rn(omf, f, __fmul2_rn(w2, a));
+    float2 b = __ffma2_rn(phg, si, Ag);
+    b = __ffma2_rn(Q, __ffma2_rn(si, eD, eD), b);
+    go = __ffma2_rn(omg, g, __fmul2_rn(w2, b));
+}
+
 // Pass 4: collision (Eqs. 22-29, Gamma_i = 1 + s_i) and push.  FP32 is
-// held to 128 registers (two 256-thread CTAs per SM; left free it took
-// 144 and ran 20% slower).
+// held to 128 registers (16 warps per SM; left free it took 144 and ran
+// 20% slower).
 template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k3_collide(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ phi,
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 2) k3_collide(const T *__restrict__ src, T *__restrict__ dst, const T *__restrict__ phi,
                            const T *__restrict__ mu, const T *__restrict__ pf_, const K3<T> P) {
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= P.N) return;
-    const Nbr3 n((int)k, P.nx, P.ny, P.nz);
+    int x, y, z;
+    if (!cell3(P, x, y, z)) return;
+    const Nbr3 n(x, y, z, P.nx, P.ny, P.nz);
+    const int k = n.k;
     T f[19], g[19];
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
@@ -208,21 +250,54 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k3_collide(const 
     const T omf = T(1) - P.itf, omg = T(1) - P.itg;
     const T phg = P.itg * m.phi;
     const T Ag = P.itg * P.alpha * __ldg(mu + k);
+    if constexpr (sizeof(T) == 4) {
+        // FP32: rest direction, then the 9 opposite pairs (2j-1, 2j) in
+        // packed f32x2 arithmetic (collide_pair3)
+        const float uZ = uF + (1.0f / 3.0f) * uR;
+        {
+            const float si = -uu15, eF = -uF, eZ = -uZ, eD = -uD, w = float(D3Q19::w(0));
+            const float fv = omf * f[0] + w * (Kf + Bf * si + P.pf * (eF + si * eZ));
+            const float Hg = (phg - float(1.0 - D3Q19::w(0)) * Ag) * float(1.0 / D3Q19::w(0));
+            const float gv = omg * g[0] + w * (Hg + phg * si + Q * (eD + si * eD));
+            dst[k] = fv;
+            dst[19 * P.NS + k] = gv;
+        }
+        const float2 mu15 = bc3(-uu15), muF = bc3(-uF), muZ = bc3(-uZ), muD = bc3(-uD);
+        const float2 Kf2 = bc3(Kf), Bf2 = bc3(Bf), pf2 = bc3(P.pf), omf2 = bc3(omf);
+        const float2 Ag2 = bc3(Ag), phg2 = bc3(phg), Q2 = bc3(Q), omg2 = bc3(omg);
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        const T cx = T(D3Q19::cx(i)), cy = T(D3Q19::cy(i)), cz = T(D3Q19::cz(i));
-        const T w = T(D3Q19::w(i));
-        const T cu = cx * ux + cy * uy + cz * uz;
-        const T si = cu * (T(3) + T(4.5) * cu) - uu15;        // s_i (Eq. 26)
-        const T eF = (cx * m.F[0] + cy * m.F[1] + cz * m.F[2]) - uF;
-        const T eR = T(1.0 / 3.0) * ((cx * gr[0] + cy * gr[1] + cz * gr[2]) - uR);
-        const T eD = (cx * D[0] + cy * D[1] + cz * D[2]) - uD;
-        const T fv = omf * f[i] + w * (Kf + Bf * si + P.pf * (eF + si * (eF + eR)));
-        const T Hg = (i == 0) ? (phg - T(1.0 - D3Q19::w(0)) * Ag) * T(1.0 / D3Q19::w(0)) : Ag;
-        const T gv = omg * g[i] + w * (Hg + phg * si + Q * (eD + si * eD));
-        const long long kd = n.o[i];
-        dst[i * P.NS + kd] = fv;
-        dst[(19 + i) * P.NS + kd] = gv;
+        for (int i = 1; i < 19; i += 2) {
+            const float cx = float(D3Q19::cx(i)), cy = float(D3Q19::cy(i)), cz = float(D3Q19::cz(i));
+            const float cu = cx * ux + cy * uy + cz * uz;
+            const float cF = cx * m.F[0] + cy * m.F[1] + cz * m.F[2];
+            const float cZ = cF + (1.0f / 3.0f) * (cx * gr[0] + cy * gr[1] + cz * gr[2]);
+            const float cD = cx * D[0] + cy * D[1] + cz * D[2];
+            float2 fo, go;
+            collide_pair3(bc3(cu), bc3(cF), bc3(cZ), bc3(cD), float(D3Q19::w(i)), mu15, muF, muZ, muD, Kf2,
+                          Bf2, pf2, omf2, Ag2, phg2, Q2, omg2, make_float2(f[i], f[i + 1]),
+                          make_float2(g[i], g[i + 1]), fo, go);
+            dst[i * P.NS + n.o[i]] = fo.x;
+            dst[(i + 1) * P.NS + n.o[i + 1]] = fo.y;
+            dst[(19 + i) * P.NS + n.o[i]] = go.x;
+            dst[(20 + i) * P.NS + n.o[i + 1]] = go.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            const T cx = T(D3Q19::cx(i)), cy = T(D3Q19::cy(i)), cz = T(D3Q19::cz(i));
+            const T w = T(D3Q19::w(i));
+            const T cu = cx * ux + cy * uy + cz * uz;
+            const T si = cu * (T(3) + T(4.5) * cu) - uu15;        // s_i (Eq. 26)
+            const T eF = (cx * m.F[0] + cy * m.F[1] + cz * m.F[2]) - uF;
+            const T eR = T(1.0 / 3.0) * ((cx * gr[0] + cy * gr[1] + cz * gr[2]) - uR);
+            const T eD = (cx * D[0] + cy * D[1] + cz * D[2]) - uD;
+            const T fv = omf * f[i] + w * (Kf + Bf * si + P.pf * (eF + si * (eF + eR)));
+            const T Hg = (i == 0) ? (phg - T(1.0 - D3Q19::w(0)) * Ag) * T(1.0 / D3Q19::w(0)) : Ag;
+            const T gv = omg * g[i] + w * (Hg + phg * si + Q * (eD + si * eD));
+            const long long kd = n.o[i];
+            dst[i * P.NS + kd] = fv;
+            dst[(19 + i) * P.NS + kd] = gv;
+        }
     }
 }
 

@@ -77,7 +77,8 @@ def _gpu(L, p, nz, phi, u, steps, dtype):
     return out
 
 
-CASES = [(12, 10, 9, 1, 0.0), (8, 6, 5, 2, 2e-5), (16, 8, 12, 3, -1e-5)]
+# the last case: a deeper grid with odd sizes (33 planes)
+CASES = [(12, 10, 9, 1, 0.0), (8, 6, 5, 2, 2e-5), (16, 8, 12, 3, -1e-5), (10, 9, 33, 4, 1e-5)]
 
 
 @pytest.mark.parametrize("nx,ny,nz,seed,grav", CASES)
