@@ -56,17 +56,21 @@ STEP_SOURCES = ("lbm_internal.h", "lbm_kernels.cuh", "lbm_strip.cuh", "lbm_strip
                 "lbm_ops.cuh", "lbm_f64.cu", "lbm_f32.cu", "lbm_f16.cu")
 
 
-def _kernel_hash() -> str:
+# Sources of the D3Q19 step kernels and their launch.
+STEP3_SOURCES = ("lbm3_kernels.cuh", "lbm3.cu")
+
+
+def _kernel_hash(sources=STEP_SOURCES) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1507_03521_gb300", "csrc")
-    for name in STEP_SOURCES:
+    for name in sources:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def _traffic(dtype: str):
+def _traffic(dtype: str, sources=STEP_SOURCES):
     """DRAM bytes per launch of the step kernel from a committed ncu
     summary, if it was taken on the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -74,7 +78,7 @@ def _traffic(dtype: str):
         with open(path) as f:
             d = json.load(f)
         e = d.get(dtype)
-        if e and e.get("kernel_hash") == _kernel_hash():
+        if e and e.get("kernel_hash") == _kernel_hash(sources):
             return float(e["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -347,11 +351,13 @@ def measure_lagged(lbm, p, phi, args, peak, mlups_sync, dist):
 
 def measure_3d(lbm, W, args, peak, dist):
     """The D3Q19 step on the 3-D analogue of the precision workload: 256^3
-    periodic, 64 spherical droplets, rho ratio 100, FP32; four launches per
-    step.  Algorithmic bytes: 19 + 19 FP32 populations read and written,
-    304 B per cell."""
+    periodic, 64 spherical droplets (the same volume fraction at --n3),
+    rho ratio 100, FP32; four launches per step.  Algorithmic bytes: 19 + 19
+    FP32 populations read and written, 304 B per cell."""
     import torch
-    p, phi, nz = W.precision3d()
+    n3 = args.n3
+    drops = max(1, round(64 * (n3 / 256) ** 3))
+    p, phi, nz = W.precision3d(n=n3, n_drops=drops)
     sim = lbm.Sim3(p, nz, "f32")
     sim.init_phi(phi)
     sim.step(args.warmup)
@@ -371,10 +377,10 @@ def measure_3d(lbm, W, args, peak, dist):
     gbs = 304 * cells / (ms / args.steps * 1e-3) / 1e9
     m0 = sim.mass()
     sim.close()
-    return {"workload": "precision3d-256^3-64-droplets-rho100", "dtype": "f32",
+    return {"workload": f"precision3d-{n3}^3-{drops}-droplets-rho100", "dtype": "f32",
             "mlups": round(mlups, 2), "ms_per_step": round(ms / args.steps, 5),
             "bytes_per_cell": 304, "hbm_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
-            "launches_per_step": 4, "traffic_per_step": _traffic("d3q19_f32"),
+            "launches_per_step": 4, "traffic_per_step": _traffic("d3q19_f32", STEP3_SOURCES) if n3 == 256 else None,
             "finite": bool(np.isfinite(m0[0]))}
 
 
@@ -428,6 +434,7 @@ def main():
     ap.add_argument("--no-slabs", action="store_true", help="skip the y-slab decomposition")
     ap.add_argument("--no-lagged", action="store_true", help="skip the lagged-grad-p variant")
     ap.add_argument("--no-3d", action="store_true", help="skip the D3Q19 workload")
+    ap.add_argument("--n3", type=int, default=256, help="side of the D3Q19 workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
