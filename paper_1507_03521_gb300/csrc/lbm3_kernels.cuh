@@ -348,8 +348,8 @@ __global__ void k3_fields(const T *__restrict__ lvl, const T *__restrict__ phi,
 // Deterministic FP64 partial sums per block (fixed order), then one block
 // folds them: out[0] = sum rho, out[1] = sum phi.
 template <class T>
-__global__ void k3_mass_partial(const T *__restrict__ lvl, double *part, const K3<T> P) {
-    __shared__ double sr[256], sp[256];
+__global__ void __launch_bounds__(256) k3_mass_partial(const T *__restrict__ lvl, double *part, const K3<T> P) {
+    __shared__ double sr[8], sp[8];
     double r = 0.0, s = 0.0;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < P.N;
          k += (long long)gridDim.x * blockDim.x) {
@@ -359,19 +359,26 @@ __global__ void k3_mass_partial(const T *__restrict__ lvl, double *part, const K
         s += ph;
         r += (double)P.rhoB + (ph - (double)P.phiB) * (double)P.drho;
     }
-    sr[threadIdx.x] = r;
-    sp[threadIdx.x] = s;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
-            sr[threadIdx.x] += sr[threadIdx.x + h];
-            sp[threadIdx.x] += sp[threadIdx.x + h];
-        }
-        __syncthreads();
+    // warp shuffles, then the 8 warp sums in order: a fixed summation order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        r += __shfl_down_sync(0xffffffffu, r, o);
+        s += __shfl_down_sync(0xffffffffu, s, o);
     }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sr[wid] = r;
+        sp[wid] = s;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = sr[0];
-        part[2 * blockIdx.x + 1] = sp[0];
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < 8; ++i) {
+            a += sr[i];
+            b += sp[i];
+        }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
     }
 }
 
@@ -380,10 +387,10 @@ __global__ void k3_mass_partial(const T *__restrict__ lvl, double *part, const K
 // (nearest periodic image), with the counts and the volume of fluid A:
 // part[5 b + (0..4)] = sum_in, n_in, sum_out, n_out, volume.
 template <class T>
-__global__ void k3_laplace_partial(const T *__restrict__ phi, const T *__restrict__ p,
+__global__ void __launch_bounds__(256) k3_laplace_partial(const T *__restrict__ phi, const T *__restrict__ p,
                                    const K3<T> P, double beta, double kappa, double xc, double yc,
                                    double zc, double rin, double rout, double *part) {
-    __shared__ double sh[5][256];
+    __shared__ double sh[5][8];
     double acc[5] = {0, 0, 0, 0, 0};
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < P.N;
          k += (long long)gridDim.x * blockDim.x) {
@@ -415,17 +422,21 @@ __global__ void k3_laplace_partial(const T *__restrict__ phi, const T *__restric
         acc[4] += (ph - pb) / (pa - pb);
     }
 #pragma unroll
-    for (int j = 0; j < 5; ++j) sh[j][threadIdx.x] = acc[j];
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h)
+    for (int j = 0; j < 5; ++j)
 #pragma unroll
-            for (int j = 0; j < 5; ++j) sh[j][threadIdx.x] += sh[j][threadIdx.x + h];
-        __syncthreads();
-    }
+        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_down_sync(0xffffffffu, acc[j], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) sh[j][wid] = acc[j];
+    __syncthreads();
     if (threadIdx.x == 0)
 #pragma unroll
-        for (int j = 0; j < 5; ++j) part[5 * blockIdx.x + j] = sh[j][0];
+        for (int j = 0; j < 5; ++j) {
+            double a = 0.0;
+            for (int i = 0; i < 8; ++i) a += sh[j][i];
+            part[5 * blockIdx.x + j] = a;
+        }
 }
 
 // Folds `nb` partial records of `w` doubles in a fixed order.
