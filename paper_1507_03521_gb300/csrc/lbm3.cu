@@ -175,7 +175,7 @@ struct lbm3_sim {
         const K3<T> P = make_k3<T>(d, nz, L);
         lbm3::k3_mass_partial<T><<<kParts, 256, 0, stream>>>(reinterpret_cast<const T *>(level(cur)),
                                                               part(), P);
-        lbm3::k3_fold<<<1, 32, 0, stream>>>(part(), kParts, 2, out());
+        lbm3::k3_fold<<<1, 256, 0, stream>>>(part(), kParts, 2, out());
         if (lbm_status st = cuda(cudaGetLastError(), "3-D mass")) return st;
         if (lbm_status st = cuda(cudaMemcpyAsync(h, out(), 2 * sizeof(double), cudaMemcpyDeviceToHost, stream), "mass copy"))
             return st;
@@ -190,7 +190,7 @@ struct lbm3_sim {
         lbm3::k3_laplace_partial<T><<<kParts, 256, 0, stream>>>(
             reinterpret_cast<const T *>(field(0)), reinterpret_cast<const T *>(field(2)), P, d.beta,
             d.kappa, xc, yc, zc, R - 2.0 * W, R + 2.0 * W, part());
-        lbm3::k3_fold<<<1, 32, 0, stream>>>(part(), kParts, 5, out());
+        lbm3::k3_fold<<<1, 256, 0, stream>>>(part(), kParts, 5, out());
         if (lbm_status st = cuda(cudaGetLastError(), "3-D laplace")) return st;
         if (lbm_status st = cuda(cudaMemcpyAsync(h, out(), 5 * sizeof(double), cudaMemcpyDeviceToHost, stream), "laplace copy"))
             return st;

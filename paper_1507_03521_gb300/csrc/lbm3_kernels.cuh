@@ -439,12 +439,25 @@ __global__ void __launch_bounds__(256) k3_laplace_partial(const T *__restrict__ 
         }
 }
 
-// Folds `nb` partial records of `w` doubles in a fixed order.
-__global__ void k3_fold(const double *part, int nb, int w, double *out) {
-    if (threadIdx.x < w) {
+// Folds `nb` partial records of `w` (<= 8) doubles in a fixed order, one
+// block of 256 threads: thread t sums records t, t + 256, ... in ascending
+// order, each warp folds its sums by shuffles, thread j adds the 8 warp
+// sums of total j in warp order.
+__global__ void __launch_bounds__(256) k3_fold(const double *part, int nb, int w, double *out) {
+    __shared__ double ws[8][8];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    for (int j = 0; j < w; ++j) {
+        double a = 0.0;
+        for (int b = t; b < nb; b += 256) a += part[w * b + j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) ws[wid][j] = a;
+    }
+    __syncthreads();
+    if (t < w) {
         double s = 0.0;
-        for (int b = 0; b < nb; ++b) s += part[w * b + threadIdx.x];
-        out[threadIdx.x] = s;
+        for (int k = 0; k < 8; ++k) s += ws[k][t];
+        out[t] = s;
     }
 }
 

@@ -549,14 +549,10 @@ k_adj_theta(const AdjP<T> P, AdjW<T> W, double *__restrict__ part) {
     }
 }
 
-// Adds the per-block partials, in block order, to the running totals.
-static __global__ void k_adj_accumulate(const double *__restrict__ part, int nblocks, int width,
-                                        double *__restrict__ acc) {
-    if (threadIdx.x < width) {
-        double a = 0.0;
-        for (int b = 0; b < nblocks; ++b) a += part[width * b + threadIdx.x];
-        acc[threadIdx.x] += a;
-    }
+// Adds the per-block partials (fold_partials order) to the running totals.
+static __global__ void __launch_bounds__(256) k_adj_accumulate(const double *__restrict__ part, int nblocks,
+                                                               int width, double *__restrict__ acc) {
+    fold_partials<true>(part, nblocks, width, acc);
 }
 
 }  // namespace lbm

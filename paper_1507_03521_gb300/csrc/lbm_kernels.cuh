@@ -624,14 +624,35 @@ k_laplace_partial(const T *__restrict__ Ptot, const T *__restrict__ phi, const K
     }
 }
 
-// Second stage: one thread sums the per-block partials in block order.
-static __global__ void k_reduce_final(const double *__restrict__ part, int nblocks, int width,
-                               double *__restrict__ out) {
-    if (threadIdx.x < width) {
+// Second stage of the reductions: the `width` (<= 8) totals of `nblocks`
+// per-block partial records, in a fixed order, by one block of 256
+// threads.  Thread t sums records t, t + 256, ... in ascending order, each
+// warp folds its 32 sums by shuffles, and thread j adds the 8 warp sums of
+// total j in warp order.  ADD: out[j] += total, else out[j] = total.
+template <bool ADD>
+__device__ __forceinline__ void fold_partials(const double *__restrict__ part, int nblocks, int width,
+                                              double *__restrict__ out) {
+    __shared__ double ws[8][8];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    for (int j = 0; j < width; ++j) {
         double a = 0.0;
-        for (int b = 0; b < nblocks; ++b) a += part[width * b + threadIdx.x];
-        out[threadIdx.x] = a;
+        for (int b = t; b < nblocks; b += 256) a += part[width * b + j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) ws[wid][j] = a;
     }
+    __syncthreads();
+    if (t < width) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += ws[w][t];
+        if (ADD) out[t] += s;
+        else out[t] = s;
+    }
+}
+
+static __global__ void __launch_bounds__(256) k_reduce_final(const double *__restrict__ part, int nblocks,
+                                                             int width, double *__restrict__ out) {
+    fold_partials<false>(part, nblocks, width, out);
 }
 
 }  // namespace lbm

@@ -205,7 +205,7 @@ struct OpsImpl {
                             double *out2, cudaStream_t s) {
         k_mass_partial<T, ST><<<nblocks, 256, 0, s>>>(static_cast<const char *>(lvl),
                                                       make_kp<T>(d), part);
-        k_reduce_final<<<1, 32, 0, s>>>(part, nblocks, 2, out2);
+        k_reduce_final<<<1, 256, 0, s>>>(part, nblocks, 2, out2);
         return cudaGetLastError();
     }
 
@@ -215,7 +215,7 @@ struct OpsImpl {
         k_laplace_partial<T><<<nblocks, 256, 0, s>>>(static_cast<const T *>(P),
                                                      static_cast<const T *>(phi), make_kp<T>(d),
                                                      xc, yc, rin, rout, part);
-        k_reduce_final<<<1, 32, 0, s>>>(part, nblocks, 5, out5);
+        k_reduce_final<<<1, 256, 0, s>>>(part, nblocks, 5, out5);
         return cudaGetLastError();
     }
 
@@ -296,7 +296,7 @@ struct OpsImpl {
         const int nb = adj_grid(d);
         k_adj_seed<T><<<nb, 256, 0, s>>>(static_cast<const T *>(lvl), static_cast<const T *>(target),
                                          static_cast<T *>(lam), make_ap(d, h), part(d, work));
-        k_reduce_final<<<1, 32, 0, s>>>(part(d, work), nb, 1, acc(d, work) + 2);
+        k_reduce_final<<<1, 256, 0, s>>>(part(d, work), nb, 1, acc(d, work) + 2);
         return cudaGetLastError();
     }
 
@@ -315,7 +315,7 @@ struct OpsImpl {
         k_adj_mu<T><<<nb, 256, 0, s>>>(P, W);
         k_adj_phi<T><<<nb, 256, 0, s>>>(L, P, W);
         k_adj_theta<T><<<nb, 256, 0, s>>>(P, W, part(d, work));
-        k_adj_accumulate<<<1, 32, 0, s>>>(part(d, work), nb, 2, acc(d, work));
+        k_adj_accumulate<<<1, 256, 0, s>>>(part(d, work), nb, 2, acc(d, work));
         return cudaGetLastError();
     }
 
@@ -330,7 +330,7 @@ struct OpsImpl {
         k_adj_init_b<T><<<nb, 256, 0, s>>>(static_cast<const T *>(lam0), static_cast<T *>(phi0_bar),
                                            P, W);
         k_adj_theta<T><<<nb, 256, 0, s>>>(P, W, part(d, work));
-        k_adj_accumulate<<<1, 32, 0, s>>>(part(d, work), nb, 2, acc(d, work));
+        k_adj_accumulate<<<1, 256, 0, s>>>(part(d, work), nb, 2, acc(d, work));
         return cudaGetLastError();
     }
 
