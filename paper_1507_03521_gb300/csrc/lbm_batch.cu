@@ -37,8 +37,8 @@ struct Plan {
     long long cells = 0;
     size_t state = 0;
     // work buffer layout
-    size_t doms_off = 0, items_off = 0, fields_off = 0, field_slot = 0, part_off = 0, out_off = 0,
-           work = 0;
+    size_t doms_off = 0, items_off = 0, tickets_off = 0, fields_off = 0, field_slot = 0, part_off = 0,
+           out_off = 0, work = 0;
     int max_items = 0;
 };
 
@@ -80,6 +80,8 @@ std::string make_plan(const lbm_params *prms, int n, Plan &P, const Ops **ops_ou
     w += r256((size_t)n * ops->batch_dom_bytes);
     P.items_off = w;
     w += r256((size_t)P.max_items * sizeof(BatchItem));
+    P.tickets_off = w;  // the step kernel's work-claim counter
+    w += 256;
     P.field_slot = r256((size_t)P.cells * ops->field_size);
     P.fields_off = w;
     w += 4 * P.field_slot;  // phi, ux, uy, p staging for host transfers
@@ -128,6 +130,7 @@ struct lbm_batch {
     }
     char *level(int dom, int par) { return state + P.lvl_off[par][dom]; }
     BatchItem *items() { return reinterpret_cast<BatchItem *>(work + P.items_off); }
+    unsigned long long *tickets() { return reinterpret_cast<unsigned long long *>(work + P.tickets_off); }
     char *slot(int i) { return work + P.fields_off + (size_t)i * P.field_slot; }
 };
 
@@ -164,6 +167,8 @@ lbm_status build_items(lbm_batch *b) {
     for (size_t i = 0; i < order.size(); ++i) sorted[i] = it[order[i]];
     LBMB_CK(b, cudaMemcpyAsync(b->items(), sorted.data(), sorted.size() * sizeof(BatchItem),
                                cudaMemcpyHostToDevice, b->stream));
+    // a new item count changes the tickets per step: restart the counter
+    LBMB_CK(b, cudaMemsetAsync(b->tickets(), 0, sizeof(unsigned long long), b->stream));
     LBMB_CK(b, cudaStreamSynchronize(b->stream));
     b->nitems = (int)sorted.size();
     b->items_ready = true;
@@ -175,8 +180,8 @@ lbm_status launch_step(lbm_batch *b, int parity) {
     int slots = 0;
     LBMB_CK(b, b->ops->batch_slots(&slots));
     const int grid = std::min(slots, b->nitems);
-    LBMB_CK(b, b->ops->batch_step(b->state, b->work + b->P.doms_off, b->items(), b->nitems, parity,
-                                  grid, b->stream));
+    LBMB_CK(b, b->ops->batch_step(b->state, b->work + b->P.doms_off, b->items(), b->nitems, b->tickets(),
+                                  parity, grid, b->stream));
     return LBM_OK;
 }
 

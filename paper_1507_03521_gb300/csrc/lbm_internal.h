@@ -70,7 +70,7 @@ struct Ops {
     void (*batch_fill_dom)(void *host_dst, const Derived &, long long off0, long long off1);
     cudaError_t (*batch_slots)(int *slots);  // resident CTAs of one batch launch
     cudaError_t (*batch_step)(char *state, const void *doms, const BatchItem *items, int nitems,
-                              int parity, int grid, cudaStream_t s);
+                              unsigned long long *tickets, int parity, int grid, cudaStream_t s);
     // adjoint (plain FP64 / FP32 storage only; null otherwise)
     cudaError_t (*adj_seed)(const Derived &, const AdjHost &, const void *lvl, const void *target,
                             void *lam, void *work, cudaStream_t s);

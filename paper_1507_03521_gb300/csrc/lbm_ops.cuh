@@ -254,12 +254,12 @@ struct OpsImpl {
     }
 
     static cudaError_t batch_step(char *state, const void *doms, const BatchItem *items, int nitems,
-                                  int parity, int grid, cudaStream_t s) {
+                                  unsigned long long *tickets, int parity, int grid, cudaStream_t s) {
         int slots = 0;
         cudaError_t e = batch_slots(&slots);  // also sets the shared-memory attribute
         if (e != cudaSuccess) return e;
         k_strip_batch<T, ST, SW, DEPTH><<<grid, NT, SM::bytes, s>>>(
-            state, static_cast<const BatchDom<T> *>(doms), items, nitems, parity);
+            state, static_cast<const BatchDom<T> *>(doms), items, nitems, tickets, parity);
         return cudaGetLastError();
     }
 

@@ -743,8 +743,10 @@ k_strip(const char *__restrict__ src, char *__restrict__ dst, const __grid_const
 
 // A batch advances many independent domains (each with its own size and
 // parameters) in one launch per step.  Work items are (domain, strip,
-// segment); a persistent grid walks the item list, which the host sorts by
-// decreasing cost.
+// segment), sorted by the host by decreasing cost; the CTAs of a
+// persistent grid claim them in that order from a ticket counter, so a CTA
+// that finishes early takes the next item (longest items first, then the
+// short ones fill the tail).
 template <class T>
 struct BatchDom {
     KP<T> kp;
@@ -754,20 +756,34 @@ struct BatchDom {
 template <class T, class ST, int SW, int DEPTH>
 __global__ void __launch_bounds__(strip_threads(SW), (StripSmem<T, ST, SW, DEPTH>::MINB))
 k_strip_batch(char *__restrict__ state, const BatchDom<T> *__restrict__ doms,
-              const BatchItem *__restrict__ items, int nitems, int parity) {
+              const BatchItem *__restrict__ items, int nitems, unsigned long long *__restrict__ tickets,
+              int parity) {
     extern __shared__ __align__(16) char smem_raw[];
     __shared__ KP<T> sP;
     __shared__ long long sOff[2];
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-        const BatchItem w = items[it];
-        __syncthreads();  // the previous item is done with sP
+    __shared__ BatchItem sW;
+    __shared__ int sIt;
+    // A step hands out nitems + gridDim.x tickets: ticket mod that count is
+    // an item index, or (>= nitems) the one stop ticket of a CTA.  Every CTA
+    // stops at its first stop ticket, so each step takes exactly that many
+    // and the counter needs no reset between stream-ordered launches.
+    const unsigned long long per_step = (unsigned long long)nitems + gridDim.x;
+    for (;;) {
+        __syncthreads();  // the previous item is done with sP, sW and sIt
         if (threadIdx.x == 0) {
-            sP = doms[w.dom].kp;
-            sOff[0] = doms[w.dom].off[parity];
-            sOff[1] = doms[w.dom].off[1 - parity];
+            const int it = (int)(atomicAdd(tickets, 1ULL) % per_step);
+            sIt = it;
+            if (it < nitems) {
+                const BatchItem w = items[it];
+                sW = w;
+                sP = doms[w.dom].kp;
+                sOff[0] = doms[w.dom].off[parity];
+                sOff[1] = doms[w.dom].off[1 - parity];
+            }
         }
         __syncthreads();
-        strip_body<T, ST, SW, DEPTH>(state + sOff[0], state + sOff[1], sP, w.x0, w.ys, w.ye,
+        if (sIt >= nitems) break;
+        strip_body<T, ST, SW, DEPTH>(state + sOff[0], state + sOff[1], sP, sW.x0, sW.ys, sW.ye,
                                      smem_raw);
     }
 }
