@@ -233,9 +233,16 @@ LBM_API lbm_status lbm_batch_bind_buffers(lbm_batch *b, void *state, size_t stat
 /* Equilibrium initial state of every domain from the concatenated phi
  * (u = 0), device or host memory (on_host). */
 LBM_API lbm_status lbm_batch_init_phi(lbm_batch *b, const void *phi, int on_host);
-/* Advance every domain n steps: one launch per step, or, with graph replay
+/* Advance every domain n steps: per step one launch of the strip kernel,
+ * plus one of the narrow-strip kernel when some strips have at most 64
+ * active columns (forms that have one: f32, f16s, bf16s); with graph replay
  * on, two steps per replay of a captured CUDA graph. */
 LBM_API lbm_status lbm_batch_step(lbm_batch *b, int64_t n);
+/* Work items of one step: *wide for the strip kernel, *narrow for the
+ * narrow-strip kernel (0 when that launch is skipped).  Either pointer may
+ * be NULL.  Errors: LBM_ERR_ARG (null handle), LBM_ERR_STATE (no buffers
+ * bound yet). */
+LBM_API lbm_status lbm_batch_work_items(const lbm_batch *b, int *wide, int *narrow);
 /* Switch CUDA-graph replay of lbm_batch_step on (1) or off (0). */
 LBM_API lbm_status lbm_batch_set_graph(lbm_batch *b, int use_graph);
 /* Rows per work item (>= 16; default 64): the tile shape of the batch. */

@@ -1,10 +1,11 @@
 // lbm_batch.cu — the batched form of the C ABI (include/lbm.h, lbm_batch_*).
 //
 // Many independent domains (each with its own size and parameters, one
-// storage type for the whole batch) advance together: one launch of the
-// batched strip kernel per time step walks a work list of (domain, strip,
-// segment) items with a persistent grid.  Optionally the launches are
-// replayed from a CUDA graph.  Host-side bookkeeping only; every step of
+// storage type for the whole batch) advance together: per time step a
+// persistent launch of the batched strip kernel works through a list of
+// (domain, strip, segment) items, and a second one, of the narrow-strip
+// kernel, through the strips of at most 64 active columns.  Optionally the
+// launches are replayed from a CUDA graph.  Host-side bookkeeping only; every step of
 // the method runs in the kernels of lbm_strip.cuh / lbm_kernels.cuh.
 #include <cuda_runtime.h>
 
@@ -80,7 +81,7 @@ std::string make_plan(const lbm_params *prms, int n, Plan &P, const Ops **ops_ou
     w += r256((size_t)n * ops->batch_dom_bytes);
     P.items_off = w;
     w += r256((size_t)P.max_items * sizeof(BatchItem));
-    P.tickets_off = w;  // the step kernel's work-claim counter
+    P.tickets_off = w;  // the work-claim counters of the two batch kernels
     w += 256;
     P.field_slot = r256((size_t)P.cells * ops->field_size);
     P.fields_off = w;
@@ -106,7 +107,8 @@ struct lbm_batch {
     int64_t steps = 0;
     bool initialized = false;
     int seg_h = 64;
-    int nitems = 0;
+    int nitems = 0;    // items of the strip_width kernel, first in the item array
+    int nitems_n = 0;  // items of the narrow kernel, after them
     bool items_ready = false;
     bool use_graph = false;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // two steps starting at parity 0 / 1
@@ -142,46 +144,69 @@ struct lbm_batch {
 
 namespace {
 
-// Work list for segment height seg_h, sorted by decreasing cost so that the
-// persistent grid's round-robin walk balances (longest items first).
+// Work lists for segment height seg_h, each sorted by decreasing cost so
+// that the persistent grid's CTAs, claiming items in order, take the
+// longest first.  A strip of at most narrow_width active columns goes to
+// the narrow kernel's list when the form has one.
 lbm_status build_items(lbm_batch *b) {
     const int SW = b->ops->strip_width;
-    std::vector<BatchItem> it;
-    std::vector<long long> cost;
+    const int NW = b->ops->batch_step_narrow ? b->ops->narrow_width : 0;
+    std::vector<BatchItem> it[2];
+    std::vector<long long> cost[2];
     for (size_t i = 0; i < b->P.d.size(); ++i) {
         const Derived &d = b->P.d[i];
         const int nseg = (d.ny + b->seg_h - 1) / b->seg_h;
         const int h = (d.ny + nseg - 1) / nseg;  // balanced segment height
-        for (int x0 = 0; x0 < d.nx; x0 += SW)
+        for (int x0 = 0; x0 < d.nx; x0 += SW) {
+            const int w = std::min(SW, d.nx - x0);
+            const int k = w <= NW ? 1 : 0;
             for (int ys = 0; ys < d.ny; ys += h) {
                 const int ye = std::min(ys + h, d.ny);
-                it.push_back(BatchItem{(int)i, x0, ys, ye});
-                cost.push_back((long long)std::min(SW, d.nx - x0) * (ye - ys + 6));
+                it[k].push_back(BatchItem{(int)i, x0, ys, ye});
+                cost[k].push_back((long long)w * (ye - ys + 6));
             }
+        }
     }
-    if ((int)it.size() > b->P.max_items) return b->fail(LBM_ERR_ARG, "segment height too small");
-    std::vector<int> order(it.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
-    std::vector<BatchItem> sorted(it.size());
-    for (size_t i = 0; i < order.size(); ++i) sorted[i] = it[order[i]];
+    if ((int)(it[0].size() + it[1].size()) > b->P.max_items)
+        return b->fail(LBM_ERR_ARG, "segment height too small");
+    std::vector<BatchItem> sorted;
+    for (int k = 0; k < 2; ++k) {
+        std::vector<int> order(it[k].size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[k][a] > cost[k][c]; });
+        for (int o : order) sorted.push_back(it[k][o]);
+    }
     LBMB_CK(b, cudaMemcpyAsync(b->items(), sorted.data(), sorted.size() * sizeof(BatchItem),
                                cudaMemcpyHostToDevice, b->stream));
-    // a new item count changes the tickets per step: restart the counter
-    LBMB_CK(b, cudaMemsetAsync(b->tickets(), 0, sizeof(unsigned long long), b->stream));
+    // new item counts change the tickets per step: restart both counters
+    LBMB_CK(b, cudaMemsetAsync(b->tickets(), 0, 2 * sizeof(unsigned long long), b->stream));
     LBMB_CK(b, cudaStreamSynchronize(b->stream));
-    b->nitems = (int)sorted.size();
+    b->nitems = (int)it[0].size();
+    b->nitems_n = (int)it[1].size();
     b->items_ready = true;
     b->drop_graphs();
     return LBM_OK;
 }
 
+// One step: the strip_width kernel, then the narrow kernel when it has
+// items, on the batch's stream.  (Running the narrow kernel on a second,
+// forked stream was measured: no gain over the sequential order.)
 lbm_status launch_step(lbm_batch *b, int parity) {
-    int slots = 0;
-    LBMB_CK(b, b->ops->batch_slots(&slots));
-    const int grid = std::min(slots, b->nitems);
-    LBMB_CK(b, b->ops->batch_step(b->state, b->work + b->P.doms_off, b->items(), b->nitems, b->tickets(),
-                                  parity, grid, b->stream));
+    const void *doms = b->work + b->P.doms_off;
+    if (b->nitems > 0) {
+        int slots = 0;
+        LBMB_CK(b, b->ops->batch_slots(&slots));
+        const int grid = std::min(slots, b->nitems);
+        LBMB_CK(b, b->ops->batch_step(b->state, doms, b->items(), b->nitems, b->tickets(), parity, grid,
+                                      b->stream));
+    }
+    if (b->nitems_n > 0) {
+        int slots = 0;
+        LBMB_CK(b, b->ops->batch_slots_narrow(&slots));
+        const int grid = std::min(slots, b->nitems_n);
+        LBMB_CK(b, b->ops->batch_step_narrow(b->state, doms, b->items() + b->nitems, b->nitems_n,
+                                             b->tickets() + 1, parity, grid, b->stream));
+    }
     return LBM_OK;
 }
 
@@ -248,8 +273,9 @@ lbm_status lbm_batch_bind_buffers(lbm_batch *b, void *state, size_t state_bytes,
     b->state = static_cast<char *>(state);
     b->work = static_cast<char *>(work);
     b->drop_graphs();
-    int slots = 0;  // sets the kernel's shared-memory attribute outside any capture
+    int slots = 0;  // sets the kernels' shared-memory attribute outside any capture
     LBMB_CK(b, b->ops->batch_slots(&slots));
+    if (b->ops->batch_step_narrow) LBMB_CK(b, b->ops->batch_slots_narrow(&slots));
     // domain table
     const size_t db = b->ops->batch_dom_bytes;
     std::vector<char> host(b->P.d.size() * db);
@@ -417,6 +443,14 @@ int64_t lbm_batch_cells(const lbm_batch *b) { return b ? b->P.cells : 0; }
 int64_t lbm_batch_step_count(const lbm_batch *b) { return b ? b->steps : 0; }
 
 int lbm_batch_segment(const lbm_batch *b) { return b ? b->seg_h : 0; }
+
+lbm_status lbm_batch_work_items(const lbm_batch *b, int *wide, int *narrow) {
+    if (!b) return LBM_ERR_ARG;
+    if (!b->items_ready) return LBM_ERR_STATE;
+    if (wide) *wide = b->nitems;
+    if (narrow) *narrow = b->nitems_n;
+    return LBM_OK;
+}
 
 const char *lbm_batch_last_error(const lbm_batch *b) { return b ? b->err.c_str() : "null handle"; }
 

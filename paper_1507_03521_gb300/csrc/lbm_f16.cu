@@ -6,10 +6,12 @@
 namespace lbm {
 const Ops *ops_f16s() {
     using Batch = OpsImpl<float, Store16<__half>, 2, 128, 2>;
-    return OpsImpl<float, Store16<__half>, 2, 120, 2>::ops_batch_from<Batch>("f16s");
+    using Narrow = OpsImpl<float, Store16<__half>, 2, 64, 2>;
+    return OpsImpl<float, Store16<__half>, 2, 120, 2>::ops_batch_from<Batch, Narrow>("f16s");
 }
 const Ops *ops_bf16s() {
     using Batch = OpsImpl<float, Store16<__nv_bfloat16>, 2, 128, 2>;
-    return OpsImpl<float, Store16<__nv_bfloat16>, 2, 120, 2>::ops_batch_from<Batch>("bf16s");
+    using Narrow = OpsImpl<float, Store16<__nv_bfloat16>, 2, 64, 2>;
+    return OpsImpl<float, Store16<__nv_bfloat16>, 2, 120, 2>::ops_batch_from<Batch, Narrow>("bf16s");
 }
 }  // namespace lbm

@@ -6,6 +6,7 @@
 namespace lbm {
 const Ops *ops_f32() {
     using Batch = OpsImpl<float, PlainStore<float>, 2, 128, 1>;
-    return OpsImpl<float, PlainStore<float>, 2, 120, 1>::ops_batch_from<Batch>("f32");
+    using Narrow = OpsImpl<float, PlainStore<float>, 2, 64, 1>;
+    return OpsImpl<float, PlainStore<float>, 2, 120, 1>::ops_batch_from<Batch, Narrow>("f32");
 }
 }  // namespace lbm

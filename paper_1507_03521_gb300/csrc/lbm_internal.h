@@ -78,6 +78,12 @@ struct Ops {
                             const void *lam_next, void *lam, void *work, cudaStream_t s);
     cudaError_t (*adj_init)(const Derived &, const AdjHost &, const void *phi0, const void *lam0,
                             void *phi0_bar, void *work, cudaStream_t s);
+    // narrow batch kernel for strips of at most narrow_width active columns
+    // (0 and null: none; every strip then runs at strip_width)
+    int narrow_width;
+    cudaError_t (*batch_slots_narrow)(int *slots);
+    cudaError_t (*batch_step_narrow)(char *state, const void *doms, const BatchItem *items, int nitems,
+                                     unsigned long long *tickets, int parity, int grid, cudaStream_t s);
 };
 
 const Ops *ops_f64();

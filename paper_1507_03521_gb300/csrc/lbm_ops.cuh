@@ -338,27 +338,35 @@ struct OpsImpl {
 
     // The launcher table; the batched form's launchers come from B, which
     // may be this type at another strip width.
-    template <class B>
+    template <class B, class BN = void>
     static Ops table(const char *name) {
-        return Ops{name,        sizeof(T),   &level_bytes, &ST::slot_span,
-                   &step,       &fields,     &init,        &mass,
-                   &laplace,    B::kSW,      &strip_ok,    sizeof(BatchDom<T>),
-                   &B::batch_fill_dom,       &B::batch_slots,   &B::batch_step,
-                   kPlain ? &adj_seed : nullptr, kPlain ? &adj_step : nullptr,
-                   kPlain ? &adj_init : nullptr};
+        Ops o{name,        sizeof(T),   &level_bytes, &ST::slot_span,
+              &step,       &fields,     &init,        &mass,
+              &laplace,    B::kSW,      &strip_ok,    sizeof(BatchDom<T>),
+              &B::batch_fill_dom,       &B::batch_slots,   &B::batch_step,
+              kPlain ? &adj_seed : nullptr, kPlain ? &adj_step : nullptr,
+              kPlain ? &adj_init : nullptr, 0, nullptr, nullptr};
+        if constexpr (!std::is_same<BN, void>::value) {
+            o.narrow_width = BN::kSW;
+            o.batch_slots_narrow = &BN::batch_slots;
+            o.batch_step_narrow = &BN::batch_step;
+        }
+        return o;
     }
     static const Ops *ops(const char *name) {
         static const Ops o = table<OpsImpl>(name);
         return &o;
     }
-    // Single domains and slabs at this strip width, batches at B's.  The
-    // batch's domains have widths that are multiples of 32, which whole-warp
-    // strips tile exactly; a strip width chosen for single pass per step
-    // (not a multiple of 32) would leave a narrow remainder strip in most
-    // of them.
-    template <class B>
+    // Single domains and slabs at this strip width, batches at B's, and the
+    // batches' remainder strips of at most BN's width at BN's.  The batch's
+    // domains have widths that are multiples of 32, which whole-warp strips
+    // tile exactly; a strip width chosen for single pass per step (not a
+    // multiple of 32) would leave a narrow remainder strip in most of them.
+    // A remainder of 64 columns or fewer on a 128-column CTA would leave
+    // half its threads or more idle: BN's CTAs are sized to it.
+    template <class B, class BN = void>
     static const Ops *ops_batch_from(const char *name) {
-        static const Ops o = table<B>(name);
+        static const Ops o = table<B, BN>(name);
         return &o;
     }
 };

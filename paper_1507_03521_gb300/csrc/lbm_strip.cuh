@@ -742,9 +742,9 @@ k_strip(const char *__restrict__ src, char *__restrict__ dst, const __grid_const
 // ---------------------------------------------------------------- batches
 
 // A batch advances many independent domains (each with its own size and
-// parameters) in one launch per step.  Work items are (domain, strip,
-// segment), sorted by the host by decreasing cost; the CTAs of a
-// persistent grid claim them in that order from a ticket counter, so a CTA
+// parameters) with one persistent launch per strip width per step.  Work
+// items are (domain, strip, segment), sorted by the host by decreasing
+// cost; the CTAs claim them in that order from a ticket counter, so a CTA
 // that finishes early takes the next item (longest items first, then the
 // short ones fill the tail).
 template <class T>

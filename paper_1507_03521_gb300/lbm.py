@@ -31,7 +31,7 @@ EXPORTS = ["lbm_version", "lbm_buffer_sizes", "lbm_create", "lbm_bind_buffers", 
            "lbm_batch_buffer_sizes", "lbm_batch_create", "lbm_batch_bind_buffers",
            "lbm_batch_init_phi", "lbm_batch_step", "lbm_batch_set_graph", "lbm_batch_set_segment",
            "lbm_batch_autotune", "lbm_batch_fields", "lbm_batch_mass", "lbm_batch_cells",
-           "lbm_batch_step_count", "lbm_batch_segment", "lbm_batch_last_error",
+           "lbm_batch_step_count", "lbm_batch_segment", "lbm_batch_work_items", "lbm_batch_last_error",
            "lbm_batch_destroy", "lbm_adj_work_bytes", "lbm_adj_reset", "lbm_adj_seed",
            "lbm_adj_step", "lbm_adj_init", "lbm_adj_grads",
            "lbm_slabs_buffer_sizes", "lbm_slabs_create", "lbm_slabs_bind_buffers",
@@ -140,6 +140,8 @@ def load(path: str = LIB_PATH):
     lib.lbm_batch_step_count.argtypes = [_vp]
     lib.lbm_batch_segment.restype = ctypes.c_int
     lib.lbm_batch_segment.argtypes = [_vp]
+    lib.lbm_batch_work_items.restype = ctypes.c_int
+    lib.lbm_batch_work_items.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.lbm_batch_last_error.restype = ctypes.c_char_p
     lib.lbm_batch_last_error.argtypes = [_vp]
     lib.lbm_batch_destroy.restype = None
@@ -560,7 +562,8 @@ class Sim3:
 
 
 class Batch:
-    """Many independent domains advanced by one launch per step.
+    """Many independent domains advanced together (one persistent launch per
+    strip width per step).
 
     ``params_list``: parameter dicts (every nx a multiple of 8); ``dtype``
     shared by all.  Runs on its own torch stream so that CUDA-graph replay
@@ -626,6 +629,12 @@ class Batch:
     @property
     def segment(self) -> int:
         return self._lib.lbm_batch_segment(self._h)
+
+    def work_items(self):
+        """(items of the strip kernel, items of the narrow-strip kernel) per step."""
+        w, n = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.lbm_batch_work_items(self._h, ctypes.byref(w), ctypes.byref(n)))
+        return w.value, n.value
 
     def init_phi(self, phis):
         import torch

@@ -1,4 +1,4 @@
-"""The batched form (one launch per step over many domains) against the
+"""The batched form (persistent launches over many domains per step) against the
 single-domain path and the oracle."""
 import numpy as np
 import pytest
@@ -54,6 +54,52 @@ def test_batch_equals_single_domain_runs(L, dtype, graph):
         sm, st = s.mass()
         assert m[i] == sm and t[i] == st
     assert b.step_count == 7
+    b.close()
+
+
+def test_batch_item_split_between_strip_widths(L):
+    """Strips of at most 64 active columns go to the narrow kernel (forms
+    that have one); FP64 runs every strip at its single strip width."""
+    doms = _mixed()
+    widths = [p["nx"] for p, _ in doms]
+    b = L.Batch([p for p, _ in doms], "f32")
+    b.set_segment(64)
+    wide, narrow = b.work_items()
+    want_w = want_n = 0
+    for (p, _), nx in zip(doms, widths):
+        nseg = -(-p["ny"] // 64)
+        for x0 in range(0, nx, 128):
+            if nx - x0 <= 64:
+                want_n += nseg
+            else:
+                want_w += nseg
+    assert (wide, narrow) == (want_w, want_n) and narrow > 0
+    b.close()
+    b = L.Batch([p for p, _ in doms], "f64")
+    assert b.work_items()[1] == 0
+    b.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_of_narrow_domains_only(L, graph):
+    """Every strip narrow (widths 8 .. 64): the 128-column launch is
+    skipped, and each domain is still bit-identical to stepping it alone."""
+    doms = W.batch_domains(n=6, seed=91, sides=(64,))
+    for nx, seed in ((8, 1), (40, 2), (56, 3)):
+        p, phi, _, _ = W.small_case(nx, 30, seed=seed)
+        doms.append((p, phi))
+    b = L.Batch([p for p, _ in doms], "f32", graph=graph)
+    assert b.work_items()[0] == 0 and b.work_items()[1] > 0
+    b.init_phi([phi for _, phi in doms])
+    b.step(5)
+    got = b.fields()
+    for i, (p, phi) in enumerate(doms):
+        s = L.Sim(p, "f32")
+        s.init_phi(phi)
+        s.step(5)
+        ref = s.fields(("phi", "ux", "uy", "p"))
+        for k in ("phi", "ux", "uy", "p"):
+            assert np.array_equal(got[i][k].cpu().numpy(), ref[k].cpu().numpy()), (i, k)
     b.close()
 
 
