@@ -564,24 +564,28 @@ def main():
     sim.init_phi_host(phi_h)
     sim.step(args.warmup)
     sim.fields_host(out=outs)
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    t0 = time.perf_counter()
-    sim.init_phi_host(phi_h)
-    sim.step(args.steps)
-    sim.fields_host(out=outs)
-    sim.mass()
-    t_e2e = time.perf_counter() - t0
+    # the whole job three times, the median reported (a ~0.1 s region with
+    # host transfers varies by several per cent from run to run)
+    times = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        sim.init_phi_host(phi_h)
+        sim.step(args.steps)
+        sim.fields_host(out=outs)
+        sim.mass()
+        times.append(time.perf_counter() - t0)
     sim.close()
-    t_e2e = max_over_ranks(t_e2e, dist, "cuda")
+    t_e2e = max_over_ranks(sorted(times)[1], dist, "cuda")
     h2d = phi_h.nbytes
     d2h = sum(v.nbytes for v in outs.values()) + 16
     line["e2e"] = {"value": round(cells * args.steps * world / t_e2e / 1e6, 2), "unit": "MLUPS",
                    "h2d_bytes_per_step": round(h2d / args.steps, 1),
                    "d2h_bytes_per_step": round(d2h / args.steps, 1),
                    "note": "one C-ABI job: phi0 from pinned host memory, init, steps, "
-                           "4 fields + mass back to host; bytes are per step of the job"}
+                           "4 fields + mass back to host; median of 3 jobs; bytes are per step of the job"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
