@@ -148,6 +148,12 @@ __device__ __forceinline__ T tgather(const Nb<T> &B, int x, int y, bool extrap, 
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < (N); \
          k += (long long)gridDim.x * blockDim.x)
 
+// Row of cell k (row length nx): a 32-bit division whenever k fits in an
+// int (every grid below 2^31 cells), the 64-bit one otherwise.
+__device__ __forceinline__ int row_of(long long k, int nx) {
+    return k <= 0x7fffffffLL ? (int)k / nx : (int)(k / nx);
+}
+
 // ----------------------------------------------------- forward recompute
 
 // phi, rho, and (temporarily) sum f, j in A_P, A_UX, A_UY.
@@ -188,7 +194,7 @@ __global__ void k_adj_f1(const AdjP<T> P, AdjW<T> W) {
     const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
     const long long N = (long long)P.k.nx * P.k.ny;
     ADJ_LOOP(k, N) {
-        const int y = (int)(k / B.nx), x = (int)(k - (long long)y * B.nx);
+        const int y = row_of(k, B.nx), x = (int)(k - (long long)y * B.nx);
         const T ph = W[A_PHI][k];
         const T lap = lap_g(W[A_PHI], B, x, y);
         const T q = (ph - P.k.phiA) * (ph - P.k.phiB) * (ph - P.k.phibar);
@@ -207,7 +213,7 @@ __global__ void k_adj_f2(const AdjP<T> P, AdjW<T> W) {
     const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
     const long long N = (long long)P.k.nx * P.k.ny;
     ADJ_LOOP(k, N) {
-        const int y = (int)(k / B.nx), x = (int)(k - (long long)y * B.nx);
+        const int y = row_of(k, B.nx), x = (int)(k - (long long)y * B.nx);
         T gx, gy;
         grad_g(W[A_MU], B, x, y, false, gx, gy);
         const T lm = lap_g(W[A_MU], B, x, y);
@@ -234,7 +240,7 @@ __global__ void k_adj_f3(const AdjP<T> P, AdjW<T> W) {
     const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
     const long long N = (long long)P.k.nx * P.k.ny;
     ADJ_LOOP(k, N) {
-        const int y = (int)(k / B.nx), x = (int)(k - (long long)y * B.nx);
+        const int y = row_of(k, B.nx), x = (int)(k - (long long)y * B.nx);
         T gx, gy;
         grad_g(W[A_P], B, x, y, true, gx, gy);
         W[A_GPX][k] = gx;
@@ -254,13 +260,18 @@ __global__ void k_adj_collide(const T *__restrict__ lam_next, T *__restrict__ la
     const long long N = (long long)P.k.nx * P.k.ny, NS = P.k.NS;
     const KP<T> &K = P.k;
     ADJ_LOOP(k, N) {
-        const int y = (int)(k / B.nx), x = (int)(k - (long long)y * B.nx);
+        const int y = row_of(k, B.nx), x = (int)(k - (long long)y * B.nx);
         const T phi = W[A_PHI][k], rho = W[A_RHO][k], mu = W[A_MU][k], p = W[A_P][k];
         const T ux = W[A_UX][k], uy = W[A_UY][k], Fx = W[A_FX][k], Fy = W[A_FY][k];
         const T grx = K.drho * W[A_GPHX][k], gry = K.drho * W[A_GPHY][k];
         const T lm = W[A_LMU][k], gpx = W[A_GPX][k], gpy = W[A_GPY][k];
         const T uu = ux * ux + uy * uy;
         const T q = -T(3) * phi / rho;
+        // per-cell quotients, hoisted out of the direction loop (divisions
+        // are many instructions each; by 3 they become a multiply by 1/3)
+        const T c13 = T(1.0 / 3.0);
+        const T rho3 = rho * c13, grx3 = grx * c13, gry3 = gry * c13;
+        const T m3r = -T(3) / rho, p3r2 = T(3) * phi / (rho * rho);
         const T Dx = gpx - Fx, Dy = gpy - Fy;
         T bp = 0, brho = 0, bphi = 0, bmu = 0, bux = 0, buy = 0, bFx = 0, bFy = 0, bgrx = 0,
           bgry = 0, blm = 0, bgpx = 0, bgpy = 0, balpha = 0, bgl = 0;
@@ -295,8 +306,8 @@ __global__ void k_adj_collide(const T *__restrict__ lam_next, T *__restrict__ la
             T bs = 0;
             // f^eq_i = w (p + rho s / 3)   (Eq. 24)
             bp += w * beq;
-            brho += w * s / T(3) * beq;
-            bs += w * rho / T(3) * beq;
+            brho += w * s * c13 * beq;
+            bs += w * rho3 * beq;
             // g^eq_i = H_i + w phi s   (Eqs. 25, 27)
             if (i == 0) {
                 bphi += bgeq;
@@ -310,13 +321,13 @@ __global__ void k_adj_collide(const T *__restrict__ lam_next, T *__restrict__ la
             bs += w * phi * bgeq;
             // F_i = (c - u).[w (1 + s) F + w s grad rho / 3] - w rho gamma lambda lap mu / 3
             const T eF = ex * Fx + ey * Fy, eR = ex * grx + ey * gry;
-            const T Ax = w * (T(1) + s) * Fx + w * s * grx / T(3);
-            const T Ay = w * (T(1) + s) * Fy + w * s * gry / T(3);
+            const T Ax = w * (T(1) + s) * Fx + w * s * grx3;
+            const T Ay = w * (T(1) + s) * Fy + w * s * gry3;
             bFx += w * (T(1) + s) * ex * bF;
             bFy += w * (T(1) + s) * ey * bF;
-            bgrx += w * s / T(3) * ex * bF;
-            bgry += w * s / T(3) * ey * bF;
-            bs += w * (eF + eR / T(3)) * bF;
+            bgrx += w * s * c13 * ex * bF;
+            bgry += w * s * c13 * ey * bF;
+            bs += w * (eF + eR * c13) * bF;
             bux += -Ax * bF;
             buy += -Ay * bF;
             brho += -w / T(3) * K.gl * lm * bF;
@@ -325,8 +336,8 @@ __global__ void k_adj_collide(const T *__restrict__ lam_next, T *__restrict__ la
             // G_i = q w (1 + s) (c - u).(grad p - F), q = -phi / (cs2 rho)
             const T E = ex * Dx + ey * Dy;
             const T wg = w * (T(1) + s);
-            bphi += -T(3) / rho * wg * E * bG;
-            brho += T(3) * phi / (rho * rho) * wg * E * bG;
+            bphi += m3r * wg * E * bG;
+            brho += p3r2 * wg * E * bG;
             bs += q * w * E * bG;
             bux += -q * wg * Dx * bG;
             buy += -q * wg * Dy * bG;
@@ -365,7 +376,7 @@ __global__ void k_adj_p(T *__restrict__ lam, const AdjP<T> P, AdjW<T> W) {
     const KP<T> &K = P.k;
     const T *gbx = W[B_GPX], *gby = W[B_GPY];
     ADJ_LOOP(k, N) {
-        const int y = (int)(k / B.nx), x = (int)(k - (long long)y * B.nx);
+        const int y = row_of(k, B.nx), x = (int)(k - (long long)y * B.nx);
         const T bp = W[B_P][k] + tgather(B, x, y, true, [&](long long c, int i, T coef) {
                          return coef * T(3.0 * D2Q9::w(i)) *
                                 (T(D2Q9::cx(i)) * gbx[c] + T(D2Q9::cy(i)) * gby[c]);
@@ -410,7 +421,7 @@ __global__ void k_adj_mu(const AdjP<T> P, AdjW<T> W) {
     const long long N = (long long)P.k.nx * P.k.ny;
     const T *gx = W[B_GMUX], *gy = W[B_GMUY], *bl = W[B_LMU];
     ADJ_LOOP(k, N) {
-        const int y = (int)(k / B.nx), x = (int)(k - (long long)y * B.nx);
+        const int y = row_of(k, B.nx), x = (int)(k - (long long)y * B.nx);
         const T t = tgather(B, x, y, false, [&](long long c, int i, T coef) {
             return coef * (T(3.0 * D2Q9::w(i)) * (T(D2Q9::cx(i)) * gx[c] + T(D2Q9::cy(i)) * gy[c]) +
                            T(6.0 * D2Q9::w(i)) * bl[c]);
@@ -429,7 +440,7 @@ __global__ void k_adj_phi(T *__restrict__ lam, const AdjP<T> P, AdjW<T> W) {
     const KP<T> &K = P.k;
     const T *gx = W[B_GPHX], *gy = W[B_GPHY], *bm = W[B_MU];
     ADJ_LOOP(k, N) {
-        const int y = (int)(k / B.nx), x = (int)(k - (long long)y * B.nx);
+        const int y = row_of(k, B.nx), x = (int)(k - (long long)y * B.nx);
         const T ph = W[A_PHI][k];
         // psi''(phi) = 4 beta [(phi-a)(phi-b) + (phi-a)(phi-m) + (phi-b)(phi-m)]
         const T a = ph - K.phiA, b = ph - K.phiB, m = ph - K.phibar;
@@ -472,7 +483,7 @@ __global__ void k_adj_init_b(const T *__restrict__ lam0, T *__restrict__ phi0_ba
     const KP<T> &K = P.k;
     const T *bm = W[B_MU];
     ADJ_LOOP(k, N) {
-        const int y = (int)(k / B.nx), x = (int)(k - (long long)y * B.nx);
+        const int y = row_of(k, B.nx), x = (int)(k - (long long)y * B.nx);
         const T ph = W[A_PHI][k];
         const T a = ph - K.phiA, b = ph - K.phiB, m = ph - K.phibar;
         const T psi2 = K.beta4 * (a * b + a * m + b * m);
