@@ -85,6 +85,27 @@ def _traffic(dtype: str, sources=STEP_SOURCES):
     return None
 
 
+def _alu(dtype: str):
+    """Per cell-update arithmetic of the step kernel (ncu counts) from the
+    committed record, if it was taken on the current kernel sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_alu.json")) as f:
+            d = json.load(f)
+        if d.get("kernel_hash") == _kernel_hash():
+            return d.get(dtype)
+    except Exception:
+        pass
+    return None
+
+
+def alu_peaks(lbm):
+    """Measured FMA operations per second of this GPU (lbm_alu_peak), in G/s."""
+    try:
+        return {k: round(lbm.alu_peak(k) / 1e9, 1) for k in ("f32", "f32x2", "f64")}
+    except Exception as e:  # reported, not fatal: the peaks are context
+        return {"error": str(e)}
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -508,6 +529,17 @@ def main():
                          "launch_ms": {"mean": round(avg_launch_ms, 5), "min": round(min(per), 5),
                                        "max": round(max(per), 5)}},
             "gpu_launches": args.steps, "clocks": ck}
+    # ALU side of the roofline: measured FMA rates and the FP32 lane
+    # operations per cell-update (ncu counts) at the measured speed
+    peaks = alu_peaks(lbm)
+    line["alu_peaks_gfma_s"] = peaks
+    a32 = _alu("f32")
+    if a32 and "f32" in peaks:
+        got = a32["fp32_lane_ops"] * mlups / 1e3 / world
+        line["alu"] = {"fp32_flops_per_cell": a32["fp32_flops"], "fp32_lane_ops_per_cell": a32["fp32_lane_ops"],
+                       "achieved_gops": round(got, 1), "peak_gfma": peaks["f32"],
+                       "frac": round(got / peaks["f32"], 4),
+                       "flop_per_byte": round(a32["fp32_flops"] / BYTES_PER_CELL["f32"], 2)}
 
     if not args.no_forms:
         forms = {}
@@ -520,6 +552,14 @@ def main():
             forms[dtype] = {"mlups": round(m2, 2), "ms_per_step": round(tot / ksteps, 5),
                             "hbm_gbs": round(ach2, 1), "frac": round(ach2 / peak, 4),
                             "bytes_per_cell": BYTES_PER_CELL[dtype], "traffic": _traffic(dtype)}
+            a64 = _alu("f64") if dtype == "f64" else None
+            if a64 and "f64" in peaks:
+                # FP64 add, multiply and FMA each take one FP64 pipe slot
+                got = a64["fp64_ops"] * m2 / 1e3 / world
+                forms[dtype]["roofline"] = {"bound": "alu", "achieved": round(got, 1),
+                                            "peak": peaks["f64"], "unit": "G FP64 ops/s",
+                                            "frac": round(got / peaks["f64"], 4),
+                                            "ops_per_cell": a64["fp64_ops"], "peak_kind": "measured (lbm_alu_peak)"}
             s2.close()
         # errors after the same number of steps, against the FP64 path
         errs = {}

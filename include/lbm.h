@@ -387,6 +387,20 @@ LBM_API void lbm3_destroy(lbm3_sim *s);
 LBM_API lbm_status lbm_mass_noalloc(const lbm_params *prm, const void *level, void *stream,
                                     double *mass, double *phi_total);
 
+/* ---------------------------------------------------------- ALU ceiling
+ * Measured FMA throughput of the current device, the arithmetic ceiling
+ * the step kernels are compared with.  The paper has no counterpart: it
+ * measures the GPU, not the method.
+ *   kind       0: FP32 scalar FMA, 1: FP32 FMA on packed pairs (f32x2),
+ *              2: FP64 FMA
+ *   fma_per_s  host output: FMA operations per second (FLOP/s = 2x)
+ * Launches a warm-up and a timed kernel (8 independent FMA chains per
+ * thread, 16 CTAs of 256 threads per SM) on a stream of its own and
+ * synchronises it; about 10-50 ms.  Allocates and frees 2 KB of device
+ * memory.  Errors: LBM_ERR_ARG (kind out of range, NULL output),
+ * LBM_ERR_CUDA (a failed CUDA call). */
+LBM_API lbm_status lbm_alu_peak(int kind, double *fma_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,7 @@ UNITS = {
     "lbm_batch": [],
     "lbm_slabs": [],
     "lbm3": [],
+    "lbm_peaks": [],
 }
 
 

@@ -27,7 +27,7 @@ STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_NONFI
 EXPORTS = ["lbm_version", "lbm_buffer_sizes", "lbm_create", "lbm_bind_buffers", "lbm_init_phi",
            "lbm_step", "lbm_fields", "lbm_mass", "lbm_laplace", "lbm_state_bytes",
            "lbm_get_state", "lbm_set_state", "lbm_step_count", "lbm_last_error",
-           "lbm_create_error", "lbm_destroy", "lbm_mass_noalloc",
+           "lbm_create_error", "lbm_destroy", "lbm_mass_noalloc", "lbm_alu_peak",
            "lbm_batch_buffer_sizes", "lbm_batch_create", "lbm_batch_bind_buffers",
            "lbm_batch_init_phi", "lbm_batch_step", "lbm_batch_set_graph", "lbm_batch_set_segment",
            "lbm_batch_autotune", "lbm_batch_fields", "lbm_batch_mass", "lbm_batch_cells",
@@ -112,6 +112,8 @@ def load(path: str = LIB_PATH):
     lib.lbm_destroy.argtypes = [_vp]
     lib.lbm_mass_noalloc.restype = S
     lib.lbm_mass_noalloc.argtypes = [ctypes.POINTER(CParams), _vp, _vp, _dp, _dp]
+    lib.lbm_alu_peak.restype = S
+    lib.lbm_alu_peak.argtypes = [ctypes.c_int, _dp]
     P = ctypes.POINTER(CParams)
     lib.lbm_batch_buffer_sizes.restype = S
     lib.lbm_batch_buffer_sizes.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t),
@@ -213,6 +215,17 @@ def make_params(d: dict, dtype) -> CParams:
         dtype = DTYPES[dtype]
     keys = [f[0] for f in CParams._fields_ if f[0] not in ("dtype", "gradp_lag")]
     return CParams(*[d[k] for k in keys], dtype, int(d.get("gradp_lag", 0)))
+
+
+def alu_peak(kind: str) -> float:
+    """Measured FMA operations per second of the current GPU: kind "f32"
+    (scalar), "f32x2" (packed pairs) or "f64" (lbm_alu_peak)."""
+    k = {"f32": 0, "f32x2": 1, "f64": 2}[kind]
+    out = ctypes.c_double()
+    st = load().lbm_alu_peak(k, ctypes.byref(out))
+    if st != 0:
+        raise LBMError(st, "lbm_alu_peak failed")
+    return out.value
 
 
 def buffer_sizes(d: dict, dtype):

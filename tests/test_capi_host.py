@@ -102,3 +102,11 @@ def test_handle_state_machine_without_gpu(lib):
     assert lib.lbm_step(h, 1) == -5                      # not initialised
     assert lib.lbm_step_count(h) == 0
     lib.lbm_destroy(h)
+
+
+def test_alu_peak_rejects_bad_arguments_without_gpu(lib):
+    """Argument checks come before any CUDA call."""
+    out = ctypes.c_double()
+    assert lib.lbm_alu_peak(3, ctypes.byref(out)) == -1
+    assert lib.lbm_alu_peak(-1, ctypes.byref(out)) == -1
+    assert lib.lbm_alu_peak(0, None) == -1
