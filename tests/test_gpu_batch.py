@@ -146,6 +146,51 @@ def test_batch_matches_oracle(L):
     assert finite >= 12
 
 
+def test_batch_matches_oracle_1000_steps(L):
+    """The first 16 domains of the bench's 1024-domain workload (sides up
+    to 512) and the two extremes of its size range (64 x 64, 512 x 512),
+    FP64, 1000 steps, against the OpenMP build of the oracle.  Domains
+    whose parameter set diverges must diverge on the GPU too.
+
+    Bar: the FP64 bar of the shorter runs with its 1e-12 relative term
+    taken per 100 steps, since two rounding orders drift apart step by
+    step (worst case linearly): max(1e-12 (steps / 100) S, 10 s), with S =
+    max|x|, except for p, which is relative to the lattice pressure scale
+    rho cs^2 = max(rho) / 3 when that is larger: p is a small difference of
+    populations of that size, so its rounding is set by them, not by p."""
+    from helpers import fast_oracle
+    doms = W.batch_domains(n=16, seed=1507036)
+    doms += W.batch_domains(n=1, seed=5, sides=(64,)) + W.batch_domains(n=1, seed=6, sides=(512,))
+    steps = 1000
+    b = L.Batch([p for p, _ in doms], "f64")
+    b.init_phi([phi for _, phi in doms])
+    b.step(steps)
+    got = b.fields()
+    b.close()
+    finite = 0
+    worst = []  # (error / bar, domain, field, error, max |oracle|)
+    for i, (p, phi) in enumerate(doms):
+        o = fast_oracle(p)
+        o.init_phi(phi)
+        o.step(steps)
+        ref = o.fields()
+        if not all(np.isfinite(ref[k]).all() for k in ("phi", "ux", "uy", "p")):
+            assert not np.isfinite(got[i]["phi"].cpu().numpy()).all(), i
+            continue
+        finite += 1
+        sp = oracle_spread(p, phi, None, None, steps, ref)
+        for k in ("phi", "ux", "uy", "p"):
+            S = float(np.abs(ref[k]).max())
+            if k == "p":
+                S = max(S, float(np.abs(ref["rho"]).max()) / 3.0)
+            tol = max(1e-12 * (steps / 100) * S, 10.0 * sp[k])
+            err = float(np.abs(got[i][k].cpu().numpy() - ref[k]).max())
+            worst.append((err / tol, i, k, err, float(np.abs(ref[k]).max())))
+    worst.sort(reverse=True)
+    assert worst[0][0] <= 1.0, worst[:4]
+    assert finite >= 10
+
+
 def test_batch_autotune_keeps_results(L):
     doms = _mixed()
     b = L.Batch([p for p, _ in doms], "f32", graph=True)
