@@ -1,0 +1,43 @@
+"""bench.py reports ncu-derived figures (DRAM traffic per launch, per-cell
+arithmetic) only while they were taken on the current kernel sources: the
+committed records carry a hash of those sources, and a record whose hash
+differs reads as null.  CPU only."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_records_match_current_sources():
+    # the committed records were taken on the committed kernels
+    assert bench._traffic("f32") is not None
+    assert bench._traffic("batch_f32") is not None
+    assert bench._traffic("d3q19_f32", bench.STEP3_SOURCES) is not None
+    a = bench._alu("f64")
+    assert a is not None and a["fp64_ops"] > 0
+
+
+def test_records_read_as_null_when_sources_change(monkeypatch):
+    monkeypatch.setattr(bench, "_kernel_hash", lambda sources=bench.STEP_SOURCES: "0" * 16)
+    assert bench._traffic("f32") is None
+    assert bench._traffic("d3q19_f32", bench.STEP3_SOURCES) is None
+    assert bench._alu("f32") is None
+
+
+def test_hash_covers_every_step_source():
+    csrc = os.path.join(ROOT, "paper_1507_03521_gb300", "csrc")
+    for name in bench.STEP_SOURCES + bench.STEP3_SOURCES:
+        assert os.path.exists(os.path.join(csrc, name)), name
+    assert bench._kernel_hash() != bench._kernel_hash(bench.STEP3_SOURCES)
+
+
+@pytest.mark.parametrize("key", ["f32", "f16s", "bf16s", "f64", "lag_f32", "slab_f32", "batch_f32"])
+def test_traffic_records_are_near_the_algorithmic_bytes(key):
+    import json
+    with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+        e = json.load(f)[key]
+    assert 0.9 <= e["dram_bytes_per_launch"] / e["algorithmic"] <= 1.3, key
