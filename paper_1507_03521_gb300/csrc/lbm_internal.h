@@ -19,6 +19,9 @@ struct Derived {
     // the whole domain, or one y-slab of a decomposed domain
     int slab, y0, rows, ya, yb;
     int lag;  // lagged-grad-p variant (its level carries a P slot)
+    // launches of this domain that run at the same time (the y-slabs of one
+    // step): each strip launch sizes its grid for 1/share of the GPU
+    int share = 1;
     double phiA, phiB, phibar, rhoB, drho;
     double kappa, beta, alpha, lambda, gamma;
     double grav, rhoref, tau_f, tau_g, uwb, uwt;

@@ -87,7 +87,7 @@ struct OpsImpl {
         }
         const int strips = (d.nx + SW - 1) / SW;
         const int rows = d.yb - d.ya;  // rows stepped
-        long long slots = (long long)c.per_sm * c.sms;
+        long long slots = (long long)c.per_sm * c.sms / (d.share > 1 ? d.share : 1);
         long long nseg = slots / strips;
         if (nseg < 1) nseg = 1;
         const long long max_seg = (rows + 15) / 16;

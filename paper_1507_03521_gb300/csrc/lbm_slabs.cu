@@ -100,6 +100,7 @@ std::string make_plan(const lbm_params *p, int n, const int *starts, Plan &P, co
         s.yb = P.b[i];
         s.N = (long long)s.rows * s.nx;
         s.NS = (s.N + 127) / 128 * 128;
+        s.share = n;  // the slabs of a step run at the same time
         if (!ops->strip_ok(s)) return "slabs need nx a multiple of 8";
         P.ds[i] = s;
         P.lvl_bytes[i] = r256(ops->level_bytes(s.NS));
@@ -129,7 +130,16 @@ struct lbm_slabs {
     int cur = 0;
     int64_t steps = 0;
     bool initialized = false;
+    // slabs 1..n-1 step on side streams forked from and joined to `stream`
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t fork = nullptr;
     std::string err;
+    ~lbm_slabs() {
+        for (cudaStream_t t : side) cudaStreamDestroy(t);
+        for (cudaEvent_t e : done) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+    }
     lbm_status fail(lbm_status st, const std::string &m) {
         err = m;
         return st;
@@ -241,6 +251,20 @@ lbm_status lbm_slabs_bind_buffers(lbm_slabs *s, void *state, size_t state_bytes,
     if (lbm_status st = s->cuda(cudaMemsetAsync(s->state, 0, s->P.state, s->stream), "memset"))
         return st;
     if (lbm_status st = s->cuda(cudaStreamSynchronize(s->stream), "bind")) return st;
+    if (!s->fork && n > 1) {
+        if (lbm_status st = s->cuda(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming), "event"))
+            return st;
+        for (int i = 1; i < n; ++i) {
+            cudaStream_t t = nullptr;
+            cudaEvent_t e = nullptr;
+            if (lbm_status st = s->cuda(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking), "stream"))
+                return st;
+            s->side.push_back(t);
+            if (lbm_status st = s->cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event"))
+                return st;
+            s->done.push_back(e);
+        }
+    }
     return LBM_OK;
 }
 
@@ -310,11 +334,25 @@ lbm_status lbm_slabs_step(lbm_slabs *s, int64_t n) {
     if (n < 0) return s->fail(LBM_ERR_ARG, "negative step count");
     for (int64_t t = 0; t < n; ++t) {
         const int nxt = 1 - s->cur;
+        // the slab steps are independent: slab i > 0 runs on side stream i-1,
+        // each launch sized for 1/n of the GPU (Derived::share), and the
+        // exchange waits for all of them
+        const bool par = !s->side.empty();
+        if (par) {
+            if (lbm_status st = s->cuda(cudaEventRecord(s->fork, s->stream), "fork")) return st;
+            for (cudaStream_t t : s->side)
+                if (lbm_status st = s->cuda(cudaStreamWaitEvent(t, s->fork, 0), "fork")) return st;
+        }
         for (int i = 0; i < s->n(); ++i)
-            if (lbm_status st = s->cuda(s->ops->step(s->P.ds[i], s->level(i, s->cur),
-                                                     s->level(i, nxt), s->stream),
+            if (lbm_status st = s->cuda(s->ops->step(s->P.ds[i], s->level(i, s->cur), s->level(i, nxt),
+                                                     i == 0 || !par ? s->stream : s->side[i - 1]),
                                         "slab step"))
                 return st;
+        if (par)
+            for (size_t j = 0; j < s->side.size(); ++j) {
+                if (lbm_status st = s->cuda(cudaEventRecord(s->done[j], s->side[j]), "join")) return st;
+                if (lbm_status st = s->cuda(cudaStreamWaitEvent(s->stream, s->done[j], 0), "join")) return st;
+            }
         if (s->P.boundaries > 0) {
             const Span *tab = s->tables + nxt * s->table_stride;
             // enough CTAs in x to cover the largest span (3 FP64 rows) in one pass
