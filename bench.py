@@ -107,33 +107,53 @@ def alu_peaks(lbm):
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling during the timed region: a reader thread stamps
+    each sample; entering waits until sampling is live, and only samples
+    stamped inside the region count."""
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, interval_ms: int = 20):
         self.index = index
+        self.interval_ms = interval_ms
         self.proc = None
+        self.lines = []  # (time, line)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line))
 
     def __enter__(self):
+        import threading
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.interval_ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+            t_end = time.perf_counter() + 3.0
+            while not self.lines and time.perf_counter() < t_end and self.proc.poll() is None:
+                time.sleep(0.005)
         except Exception:
             self.proc = None
+        self.t0 = time.perf_counter()
         return self
 
     def __exit__(self, *a):
+        self.t1 = time.perf_counter()
         self.out = ""
         if self.proc is not None:
+            time.sleep(self.interval_ms / 1000.0)  # the sample in flight at the end
             self.proc.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
+                self.reader.join(timeout=5)
             except Exception:
                 self.proc.kill()
+            end = self.t1 + self.interval_ms / 1000.0
+            self.out = "".join(l for t, l in self.lines if self.t0 <= t <= end)
 
     def summary(self):
         sm, mx, reasons = [], [], set()

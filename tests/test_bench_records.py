@@ -41,3 +41,22 @@ def test_traffic_records_are_near_the_algorithmic_bytes(key):
     with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
         e = json.load(f)[key]
     assert 0.9 <= e["dram_bytes_per_launch"] / e["algorithmic"] <= 1.3, key
+
+
+def test_clock_sampler_counts_samples_inside_the_region(tmp_path, monkeypatch):
+    """The clock sampler with a stand-in nvidia-smi (one sample every
+    10 ms): entering waits until sampling is live, and the samples stamped
+    inside the timed region are counted with their throttle reasons."""
+    import time
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\nwhile true; do\n"
+                    "  echo '0, 1980, 2070, 950.5, 0x4, Not Active, Not Active, Not Active, Active'\n"
+                    "  sleep 0.01\ndone\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}:{os.environ['PATH']}")
+    with bench.Clocks(0, interval_ms=10) as ck:
+        time.sleep(0.2)
+    s = ck.summary()
+    assert s["samples"] >= 5, s
+    assert s["sm_mhz"] == 1980.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
