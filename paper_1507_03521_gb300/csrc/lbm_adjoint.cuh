@@ -19,9 +19,11 @@
 //   k_adj_f0 .. k_adj_f3  recompute the forward fields of step t,
 //   k_adj_collide         streaming and collision transposed,
 //   k_adj_p               grad p transposed, then u, p, F backwards,
-//   k_adj_mu              grad mu and lap mu transposed,
+//   k_adj_mu              grad mu and lap mu transposed, and the step's
+//                         per-block (M, sigma) partial sums,
 //   k_adj_phi             grad phi and lap phi transposed, phi = sum g,
-//   k_adj_theta           per-cell (M, sigma) terms reduced in FP64.
+//   k_adj_theta           per-cell (M, sigma) terms reduced in FP64 (the
+//                         initial state's; a step's come from k_adj_mu).
 // M enters through alpha = M / (cs2 (tau_g - 1/2)) and gamma lambda with
 // lambda = M (Eq. 33); sigma through kappa and beta, both proportional to
 // sigma (Eqs. 3-4 solved), so mu = sigma mu1.
@@ -413,13 +415,44 @@ __global__ void k_adj_p(T *__restrict__ lam, const AdjP<T> P, AdjW<T> W) {
     }
 }
 
+// Block partial sums of the (M, sigma) terms, in a fixed order: each
+// thread's grid-stride sums, warp shuffles, then the 8 warp sums in order
+// (one block of 256 threads).
+__device__ __forceinline__ void adj_theta_partials(double dM, double dS, double *__restrict__ part) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dM += __shfl_down_sync(0xffffffffu, dM, o);
+        dS += __shfl_down_sync(0xffffffffu, dS, o);
+    }
+    __shared__ double wm[8], ws[8];
+    if ((threadIdx.x & 31) == 0) {
+        wm[threadIdx.x >> 5] = dM;
+        ws[threadIdx.x >> 5] = dS;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < 8; ++i) {
+            a += wm[i];
+            b += ws[i];
+        }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
 // grad mu and lap mu transposed (mirror ghosts): full adjoint of mu; the
-// sigma term mu1 * mu_bar.
+// sigma term mu1 * mu_bar.  The step's (M, sigma) terms of a cell are final
+// here (alpha_bar and (gamma lambda)_bar come from the collision and p
+// passes), so this pass also writes their per-block partial sums (the
+// reduction k_adj_theta does for the initial state).
 template <class T>
-__global__ void k_adj_mu(const AdjP<T> P, AdjW<T> W) {
+__global__ void __launch_bounds__(256) k_adj_mu(const AdjP<T> P, AdjW<T> W, double *__restrict__ part) {
     const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
     const long long N = (long long)P.k.nx * P.k.ny;
     const T *gx = W[B_GMUX], *gy = W[B_GMUY], *bl = W[B_LMU];
+    double dM = 0.0, dS = 0.0;
+    const double a1 = (double)P.alpha1, gm = (double)P.gamma;
     ADJ_LOOP(k, N) {
         const int y = row_of(k, B.nx), x = (int)(k - (long long)y * B.nx);
         const T t = tgather(B, x, y, false, [&](long long c, int i, T coef) {
@@ -427,9 +460,13 @@ __global__ void k_adj_mu(const AdjP<T> P, AdjW<T> W) {
                            T(6.0 * D2Q9::w(i)) * bl[c]);
         });
         const T bmu = W[B_MU][k] + t - T(10.0 / 3.0) * bl[k];
+        const T bsig = bmu * W[A_MU1][k];
         W[B_MU][k] = bmu;
-        W[B_SIGMA][k] = bmu * W[A_MU1][k];
+        W[B_SIGMA][k] = bsig;
+        dM += a1 * (double)W[B_ALPHA][k] + gm * (double)W[B_GL][k];
+        dS += (double)bsig;
     }
+    adj_theta_partials(dM, dS, part);
 }
 
 // grad phi and lap phi transposed: full adjoint of phi, then phi = sum g.
@@ -538,26 +575,7 @@ k_adj_theta(const AdjP<T> P, AdjW<T> W, double *__restrict__ part) {
         dM += a1 * (double)W[B_ALPHA][k] + gm * (double)W[B_GL][k];
         dS += (double)W[B_SIGMA][k];
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        dM += __shfl_down_sync(0xffffffffu, dM, o);
-        dS += __shfl_down_sync(0xffffffffu, dS, o);
-    }
-    __shared__ double wm[8], ws[8];
-    if ((threadIdx.x & 31) == 0) {
-        wm[threadIdx.x >> 5] = dM;
-        ws[threadIdx.x >> 5] = dS;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int i = 0; i < 8; ++i) {
-            a += wm[i];
-            b += ws[i];
-        }
-        part[2 * blockIdx.x] = a;
-        part[2 * blockIdx.x + 1] = b;
-    }
+    adj_theta_partials(dM, dS, part);
 }
 
 // Adds the per-block partials (fold_partials order) to the running totals.

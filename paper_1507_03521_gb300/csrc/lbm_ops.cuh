@@ -312,9 +312,8 @@ struct OpsImpl {
         k_adj_f3<T><<<nb, 256, 0, s>>>(P, W);
         k_adj_collide<T><<<nb, 256, 0, s>>>(static_cast<const T *>(lam_next), L, P, W);
         k_adj_p<T><<<nb, 256, 0, s>>>(L, P, W);
-        k_adj_mu<T><<<nb, 256, 0, s>>>(P, W);
+        k_adj_mu<T><<<nb, 256, 0, s>>>(P, W, part(d, work));  // also the (M, sigma) partials
         k_adj_phi<T><<<nb, 256, 0, s>>>(L, P, W);
-        k_adj_theta<T><<<nb, 256, 0, s>>>(P, W, part(d, work));
         k_adj_accumulate<<<1, 256, 0, s>>>(part(d, work), nb, 2, acc(d, work));
         return cudaGetLastError();
     }
