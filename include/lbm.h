@@ -195,7 +195,17 @@ LBM_API void lbm_destroy(lbm_sim *sim);
  * lam_next must differ from lam_t.  `work` is a caller-owned device buffer
  * of lbm_adj_work_bytes() bytes, 256-byte aligned, holding scratch fields
  * and the running totals (lbm_adj_reset zeroes them).  Asynchronous on the
- * handle's stream except lbm_adj_grads and a seed that returns the loss. */
+ * handle's stream except lbm_adj_grads and a seed that returns the loss.
+ * The step being differentiated is the synchronous step of Eqs. 22-32
+ * (Sec. 3) with its moment, stencil and wall rules; the paper itself has
+ * no adjoint.
+ * Errors (every call): LBM_ERR_ARG for a NULL handle, a handle that is not
+ * LBM_F64 or LBM_F32, a lagged-grad-p handle (gradp_lag != 0), a NULL or
+ * not 256-byte aligned work buffer, a NULL state/lambda/field pointer, or
+ * lam_next == lam_t; LBM_ERR_CUDA for a failed launch or copy (message in
+ * lbm_last_error).  lbm_adj_work_bytes returns LBM_ERR_ARG for a NULL
+ * output or an unsupported handle; lbm_adj_grads synchronises the stream
+ * and leaves a NULL output unwritten. */
 LBM_API lbm_status lbm_adj_work_bytes(const lbm_sim *sim, size_t *bytes);
 LBM_API lbm_status lbm_adj_reset(lbm_sim *sim, void *work);
 LBM_API lbm_status lbm_adj_seed(lbm_sim *sim, const void *state_T, const void *phi_target,
@@ -209,12 +219,14 @@ LBM_API lbm_status lbm_adj_grads(lbm_sim *sim, void *work, double *dM, double *d
 /* ------------------------------------------------------------------ batches
  * The batched form: n independent domains, each with its own size and
  * parameters (one dtype for the whole batch; every nx a multiple of 8),
- * advanced together by ONE kernel launch per time step.  The launch walks a
- * work list of (domain, 128-column strip, row segment) items with a
- * persistent grid sized to the GPU's resident CTAs; items are sorted by
- * decreasing cost.  Per-domain results are bit-identical to stepping each
- * domain alone with lbm_step.  Fields and phi are concatenated in domain
- * order, each domain row-major [ny][nx] in the field type.
+ * advanced together by one persistent kernel launch per strip width per
+ * time step.  A launch works through a list of (domain, strip, row
+ * segment) items sorted by decreasing cost, its CTAs claiming items from a
+ * counter in the work buffer: 128-column strips, and (f32, f16s, bf16s) a
+ * second list of the strips with at most 64 active columns, stepped at 64
+ * columns.  Per-domain results are bit-identical to stepping each domain
+ * alone with lbm_step.  Fields and phi are concatenated in domain order,
+ * each domain row-major [ny][nx] in the field type.
  */
 typedef struct lbm_batch lbm_batch; /* opaque handle, owned by the caller */
 
