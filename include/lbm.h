@@ -283,7 +283,10 @@ LBM_API void lbm_batch_destroy(lbm_batch *b);
  * handle's device and device-to-device copies.  Slab i owns global rows
  * a_i .. b_i - 1 and holds 3 ghost rows on each side (across the wrap when
  * periodic in y; ghost rows past a wall are not used).  A step is
- *   1. the strip kernel on each slab's own rows,
+ *   1. the strip kernel on each slab's own rows: the n launches run side by
+ *      side, slab i > 0 on a side stream forked from the handle's stream
+ *      (the handle creates n - 1 streams and n events at bind and destroys
+ *      them with itself), each sized for 1/n of the GPU,
  *   2. one copy launch moving the populations pushed across each slab edge
  *      (f and g slots 2, 5, 6 upward; 4, 7, 8 downward) to the slab that
  *      owns their row,
@@ -314,7 +317,8 @@ LBM_API lbm_status lbm_slabs_bind_buffers(lbm_slabs *s, void *state, size_t stat
 LBM_API lbm_status lbm_slabs_scatter(lbm_slabs *s, const void *level, int64_t step);
 /* Write the slabs' current state as a whole-domain level (device). */
 LBM_API lbm_status lbm_slabs_gather(lbm_slabs *s, void *level, int64_t *step);
-/* Advance n steps (asynchronous on the stream; n + 2 launches per step). */
+/* Advance n steps (asynchronous on the handle's stream, which waits for
+ * the side streams before the copies; n + 2 launches per step). */
 LBM_API lbm_status lbm_slabs_step(lbm_slabs *s, int64_t n);
 /* Rows a_i .. b_i - 1 owned by slab i. */
 LBM_API lbm_status lbm_slabs_rows(const lbm_slabs *s, int i, int *a, int *b);
