@@ -5,11 +5,45 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <atomic>
+#include <mutex>
 #include <string>
 
 #include "lbm.h"
 
 namespace lbm {
+
+// A value set up once per device (kernel attributes, occupancy) and shared
+// by every host thread that launches: the first caller on a device runs
+// the set-up under a mutex and publishes the result; later callers read it.
+// A failed set-up publishes nothing, so the next call tries again.
+template <class V>
+struct PerDevice {
+    static constexpr int kMaxDev = 64;
+    std::mutex mu;
+    std::atomic<bool> ready[kMaxDev] = {};
+    V val[kMaxDev] = {};
+    // fn(dev, V &) -> cudaError_t, called with `dev` current
+    template <class F>
+    cudaError_t get(V &out, F &&fn) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+        if (!ready[dev].load(std::memory_order_acquire)) {
+            std::lock_guard<std::mutex> lock(mu);
+            if (!ready[dev].load(std::memory_order_relaxed)) {
+                V v{};
+                e = fn(dev, v);
+                if (e != cudaSuccess) return e;
+                val[dev] = v;
+                ready[dev].store(true, std::memory_order_release);
+            }
+        }
+        out = val[dev];
+        return cudaSuccess;
+    }
+};
 
 // Host-side derived parameters of one domain (FP64).
 struct Derived {

@@ -59,32 +59,31 @@ struct OpsImpl {
     }
 
     struct StripCfg {
-        bool ready = false;
         int per_sm = 0, sms = 0;
     };
+    // Opt kernel `k` in to `smem` bytes of dynamic shared memory and read
+    // its resident CTAs per SM and the SM count of device `dev`.
+    template <class K>
+    static cudaError_t strip_cfg(K k, int smem, int dev, StripCfg &c) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.per_sm, k, NT, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        return c.per_sm < 1 ? cudaErrorInvalidConfiguration : cudaSuccess;
+    }
 
     // Opt in to the strip kernel's shared memory and size the grid to
     // one wave: strips x segments ~= resident CTAs, segments >= 16 rows.
     template <bool SLAB>
     static cudaError_t strip_grid(const Derived &d, dim3 &grid, int &seg_h) {
-        static StripCfg cfg[64];
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
+        static PerDevice<StripCfg> cfg;
+        StripCfg c;
+        cudaError_t e = cfg.get(c, [](int dev, StripCfg &v) {
+            return strip_cfg(k_strip<T, ST, SW, DEPTH, SLAB>, (int)SM::bytes, dev, v);
+        });
         if (e != cudaSuccess) return e;
-        if (dev >= 64) return cudaErrorInvalidDevice;
-        StripCfg &c = cfg[dev];
-        if (!c.ready) {
-            e = cudaFuncSetAttribute(k_strip<T, ST, SW, DEPTH, SLAB>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
-            if (e != cudaSuccess) return e;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &c.per_sm, k_strip<T, ST, SW, DEPTH, SLAB>, NT, SM::bytes);
-            if (e != cudaSuccess) return e;
-            e = cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e != cudaSuccess) return e;
-            if (c.per_sm < 1) return cudaErrorInvalidConfiguration;
-            c.ready = true;
-        }
         const int strips = (d.nx + SW - 1) / SW;
         const int rows = d.yb - d.ya;  // rows stepped
         long long slots = (long long)c.per_sm * c.sms / (d.share > 1 ? d.share : 1);
@@ -114,24 +113,12 @@ struct OpsImpl {
     using LS = LagSmem<T, ST, SW, DEPTH>;
     static size_t p_offset(long long NS) { return (ST::level_bytes(NS) + 255) & ~size_t(255); }
     static cudaError_t lag_step(const Derived &d, const void *src, void *dst, cudaStream_t s) {
-        static StripCfg cfg[64];
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
+        static PerDevice<StripCfg> cfg;
+        StripCfg c;
+        cudaError_t e = cfg.get(c, [](int dev, StripCfg &v) {
+            return strip_cfg(k_strip_lag<T, ST, SW, DEPTH>, (int)LS::bytes, dev, v);
+        });
         if (e != cudaSuccess) return e;
-        if (dev >= 64) return cudaErrorInvalidDevice;
-        StripCfg &c = cfg[dev];
-        if (!c.ready) {
-            e = cudaFuncSetAttribute(k_strip_lag<T, ST, SW, DEPTH>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LS::bytes);
-            if (e != cudaSuccess) return e;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.per_sm, k_strip_lag<T, ST, SW, DEPTH>,
-                                                              NT, LS::bytes);
-            if (e != cudaSuccess) return e;
-            e = cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e != cudaSuccess) return e;
-            if (c.per_sm < 1) return cudaErrorInvalidConfiguration;
-            c.ready = true;
-        }
         const int strips = (d.nx + SW - 1) / SW;
         long long nseg = (long long)c.per_sm * c.sms / strips;
         if (nseg < 1) nseg = 1;
@@ -150,15 +137,12 @@ struct OpsImpl {
         // Opt in to more than 48 KB of dynamic shared memory when needed,
         // once per device.
         if (TL::bytes <= 48 * 1024) return cudaSuccess;
-        static bool done[64] = {};
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return e;
-        if (dev < 64 && done[dev]) return cudaSuccess;
-        e = cudaFuncSetAttribute(k_step<T, ST, RPT, MODE>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::bytes);
-        if (e == cudaSuccess && dev < 64) done[dev] = true;
-        return e;
+        static PerDevice<int> done;
+        int v = 0;
+        return done.get(v, [](int, int &) {
+            return cudaFuncSetAttribute(k_step<T, ST, RPT, MODE>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::bytes);
+        });
     }
 
     static dim3 grid(const Derived &d) {
@@ -231,25 +215,13 @@ struct OpsImpl {
     }
 
     static cudaError_t batch_slots(int *slots) {
-        static int cache[64] = {};
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
+        static PerDevice<StripCfg> cfg;
+        StripCfg c;
+        cudaError_t e = cfg.get(c, [](int dev, StripCfg &v) {
+            return strip_cfg(k_strip_batch<T, ST, SW, DEPTH>, (int)SM::bytes, dev, v);
+        });
         if (e != cudaSuccess) return e;
-        if (dev >= 64) return cudaErrorInvalidDevice;
-        if (!cache[dev]) {
-            e = cudaFuncSetAttribute(k_strip_batch<T, ST, SW, DEPTH>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
-            if (e != cudaSuccess) return e;
-            int per_sm = 0, sms = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_strip_batch<T, ST, SW, DEPTH>,
-                                                              NT, SM::bytes);
-            if (e != cudaSuccess) return e;
-            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e != cudaSuccess) return e;
-            if (per_sm < 1) return cudaErrorInvalidConfiguration;
-            cache[dev] = per_sm * sms;
-        }
-        *slots = cache[dev];
+        *slots = c.per_sm * c.sms;
         return cudaSuccess;
     }
 

@@ -163,6 +163,8 @@ struct lbm_slabs {
     }
 };
 
+static lbm_status bind_tables(lbm_slabs *s, char *state, void *work);
+
 extern "C" {
 
 lbm_status lbm_slabs_buffer_sizes(const lbm_params *prm, int n_slabs, const int *row_starts,
@@ -206,7 +208,49 @@ lbm_status lbm_slabs_bind_buffers(lbm_slabs *s, void *state, size_t state_bytes,
         return s->fail(LBM_ERR_NOMEM, "bound buffer smaller than lbm_slabs_buffer_sizes");
     if ((reinterpret_cast<uintptr_t>(state) | reinterpret_cast<uintptr_t>(work)) & 255)
         return s->fail(LBM_ERR_ARG, "buffers must be 256-byte aligned");
-    s->state = static_cast<char *>(state);
+    const int n = s->n();
+    // Side streams and events first, into locals: they join the handle only
+    // when all n - 1 exist, so a failed bind leaves it as it was.
+    if (!s->fork && n > 1) {
+        cudaEvent_t fork = nullptr;
+        std::vector<cudaStream_t> side;
+        std::vector<cudaEvent_t> done;
+        cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        for (int i = 1; i < n && e == cudaSuccess; ++i) {
+            cudaStream_t t = nullptr;
+            e = cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking);
+            if (e != cudaSuccess) break;
+            side.push_back(t);
+            cudaEvent_t ev = nullptr;
+            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) break;
+            done.push_back(ev);
+        }
+        if (e != cudaSuccess) {
+            for (cudaStream_t t : side) cudaStreamDestroy(t);
+            for (cudaEvent_t ev : done) cudaEventDestroy(ev);
+            if (fork) cudaEventDestroy(fork);
+            return s->cuda(e, "side streams of the slab steps");
+        }
+        s->fork = fork;
+        s->side = std::move(side);
+        s->done = std::move(done);
+    }
+    // The handle counts as bound (s->state set) only once the tables are
+    // uploaded; scatter and step refuse it until then.
+    s->state = nullptr;
+    char *const st_base = static_cast<char *>(state);
+    const lbm_status bound = bind_tables(s, st_base, work);
+    s->state = bound == LBM_OK ? st_base : nullptr;
+    return bound;
+}
+
+}  // extern "C"
+
+// Builds and uploads the span tables of both parities, and clears the
+// state buffer; row addresses are taken relative to `state`.
+static lbm_status bind_tables(lbm_slabs *s, char *state, void *work) {
+    s->state = state;  // row_ptr addresses rows through it
     s->tables = reinterpret_cast<Span *>((reinterpret_cast<uintptr_t>(work) + 255) & ~uintptr_t(255));
     const int n = s->n();
     // Span tables of both parities (the level written by the step).
@@ -250,23 +294,10 @@ lbm_status lbm_slabs_bind_buffers(lbm_slabs *s, void *state, size_t state_bytes,
     // ghost rows past a wall are never read; clear everything once anyway
     if (lbm_status st = s->cuda(cudaMemsetAsync(s->state, 0, s->P.state, s->stream), "memset"))
         return st;
-    if (lbm_status st = s->cuda(cudaStreamSynchronize(s->stream), "bind")) return st;
-    if (!s->fork && n > 1) {
-        if (lbm_status st = s->cuda(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming), "event"))
-            return st;
-        for (int i = 1; i < n; ++i) {
-            cudaStream_t t = nullptr;
-            cudaEvent_t e = nullptr;
-            if (lbm_status st = s->cuda(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking), "stream"))
-                return st;
-            s->side.push_back(t);
-            if (lbm_status st = s->cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event"))
-                return st;
-            s->done.push_back(e);
-        }
-    }
-    return LBM_OK;
+    return s->cuda(cudaStreamSynchronize(s->stream), "bind");
 }
+
+extern "C" {
 
 lbm_status lbm_slabs_scatter(lbm_slabs *s, const void *level, int64_t step) {
     if (!s) return LBM_ERR_ARG;

