@@ -118,6 +118,7 @@ def _load(path: str | None = None):
     lib.orc_stencils.argtypes = [ctypes.c_int] * 4 + [_dp] * 4
     lib.orc_lattice.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dp]
     lib.orc_set_gradp_lag.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.orc_step_jitter.argtypes = [ctypes.c_void_p, ctypes.c_long, ctypes.c_ulonglong]
     lib.orc3_create.restype = ctypes.c_void_p
     lib.orc3_create.argtypes = [ctypes.POINTER(_Params), ctypes.c_int]
     lib.orc3_destroy.argtypes = [ctypes.c_void_p]
@@ -222,6 +223,11 @@ class Oracle:
 
     def step(self, n: int = 1):
         self._lib.orc_step(self._h, int(n))
+
+    def step_jitter(self, n: int, seed: int = 1):
+        """n steps, each after a random +-1 ulp change of every population
+        (a conditioning probe for the tests, not part of the scheme)."""
+        self._lib.orc_step_jitter(self._h, int(n), int(seed))
 
     @property
     def step_count(self) -> int:

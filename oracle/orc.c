@@ -46,6 +46,7 @@
  *    mu from the initial phi.
  */
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 
 /* ORC_MUTANT (default 0) plants one known mistake in the oracle so that the
@@ -442,6 +443,36 @@ void orc_step(orc_sim *s, long n) {
         stream(s);
         if (s->lag) memcpy(s->pprev, s->p, (size_t)s->N * sizeof(double));
         s->step++;
+    }
+}
+
+/* Conditioning probe for the tests; not part of the scheme.  Before each of
+ * n steps every population moves by one unit in the last place, up or down
+ * as the low bit of a counter-based hash of (seed, step, index) says (the
+ * SplitMix64 finaliser of Steele, Lea and Flood, 2014).  How far the fields
+ * then drift from an unperturbed run measures how strongly the run
+ * amplifies roundoff injected at every step, which is what a second
+ * implementation with another rounding order does to it. */
+static uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ULL;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+    return x ^ (x >> 31);
+}
+
+void orc_step_jitter(orc_sim *s, long n, unsigned long long seed) {
+    const long N9 = 9 * s->N;
+    for (long t = 0; t < n; ++t) {
+        const uint64_t base = splitmix64((uint64_t)seed ^ ((uint64_t)s->step << 32));
+        double *pop[2] = {s->f, s->g};
+        for (int b = 0; b < 2; ++b) {
+            double *a = pop[b];
+            const uint64_t off = base + (uint64_t)b * (uint64_t)N9;
+            ORC_PAR_ROWS
+            for (long q = 0; q < N9; ++q)
+                a[q] = nextafter(a[q], (splitmix64(off + (uint64_t)q) & 1) ? INFINITY : -INFINITY);
+        }
+        orc_step(s, 1);
     }
 }
 

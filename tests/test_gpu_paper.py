@@ -21,7 +21,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import check64, fast_oracle, linear_rate, mode_amplitude, oracle_spread
+from helpers import check64_long, fast_oracle, linear_rate, mode_amplitude, oracle_jitter_spread
 from paper_1507_03521_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -97,7 +97,8 @@ def test_phase_separation_linear_growth_gpu(L, gamma, dtype, tol):
 
 def test_phase_separation_paper_case(L):
     """Sec. 4.4 at Pe = 50, Cn = 4, eps = 0.1: the GPU matches the oracle
-    through the fast transient (2500 steps); over 20000 steps both gamma
+    through the fast transient (2500 steps, the long-run FP64 bar: the
+    decomposition amplifies roundoff); over 20000 steps both gamma
     separate, gamma = 4 first, sum phi stays put and the flow comes to rest."""
     first = {}
     for gamma in (1.0, 4.0):
@@ -110,8 +111,8 @@ def test_phase_separation_paper_case(L):
         o.init_phi(phi)
         o.step(2500)
         ref = o.fields()
-        check64(g, ref, oracle_spread(p, phi, None, None, 2500, ref),
-                f"phase separation gamma={gamma}")
+        check64_long(g, ref, oracle_jitter_spread(p, phi, None, None, 2500, ref),
+                     f"phase separation gamma={gamma}", 2500)
         s2 = L.Sim(p, "f64")
         s2.init_phi(phi)
         m0, t0 = s2.mass()
@@ -131,7 +132,8 @@ def test_phase_separation_paper_case(L):
 
 
 def test_bubble_rising(L):
-    """Sec. 4.3: FP64 GPU against the oracle for 300 steps, then to the
+    """Sec. 4.3: FP64 GPU against the oracle for 300 steps (the long-run FP64
+    bar), then to the
     paper's first snapshot (t = 10^4): conservation, the buoyancy impulse in
     the total momentum, mirror symmetry about x = nx/2, the bubble rising
     relative to the mean flow.  FP32 against FP64 at t = 10^4: the largest
@@ -151,7 +153,8 @@ def test_bubble_rising(L):
     o.init_phi(phi)
     o.step(300)
     ref = o.fields()
-    check64(g, ref, oracle_spread(p, phi, None, None, 300, ref), "bubble, 300 steps")
+    check64_long(g, ref, oracle_jitter_spread(p, phi, None, None, 300, ref), "bubble, 300 steps",
+                 300)
     T = 10000
     s.step(T - 300)
     fl = {k: v.cpu().numpy() for k, v in s.fields().items()}
