@@ -21,13 +21,22 @@
 
 namespace {
 
-// One block reduces up to kCellsPerBlock cells, so the scratch holds the
-// partial sums of at most kMaxBlocks blocks: grids up to 2^28 cells
-// (16384 x 16384).  2 * 4096 + 2 doubles = 64 KB + 16 B per device.
+// The scratch holds the partial sums of at most kMaxBlocks blocks.  A block
+// reduces `span` cells: N / kMaxBlocks rounded up to a multiple of 256, but
+// at least kMinSpan, so that mid-size grids still spread over many blocks
+// (a 2048 x 2048 grid gets 1024).  Spans are capped at kMaxSpan, which
+// limits grids to 2^28 cells (16384 x 16384).  2 * 4096 + 2 doubles = 64 KB
+// + 16 B per device.
 constexpr int kMaxBlocks = 4096;
-constexpr long long kCellsPerBlock = 65536;
-constexpr long long kMaxCells = (long long)kMaxBlocks * kCellsPerBlock;
+constexpr long long kMinSpan = 4096, kMaxSpan = 65536;
+constexpr long long kMaxCells = (long long)kMaxBlocks * kMaxSpan;
 constexpr int kScratchDoubles = 2 * kMaxBlocks + 2;
+
+long long block_span(long long N) {
+    long long span = (N + kMaxBlocks - 1) / kMaxBlocks;
+    span = (span + 255) / 256 * 256;
+    return span < kMinSpan ? kMinSpan : span;
+}
 
 // Per-block partials at [2b, 2b + 1]; the final sums at [2 kMaxBlocks, +1].
 // Every slot a call reads is written earlier in the same call, so nothing
@@ -36,11 +45,11 @@ static __device__ __align__(256) double g_mass_scratch[kScratchDoubles];
 
 template <class T, class ST>
 __global__ void __launch_bounds__(256)
-k_mass_noalloc_partial(const char *__restrict__ lvl, const lbm::KP<T> P,
+k_mass_noalloc_partial(const char *__restrict__ lvl, const lbm::KP<T> P, long long span,
                        double *__restrict__ scratch) {
     const long long N = (long long)P.nx * P.ny;
-    const long long b0 = (long long)blockIdx.x * kCellsPerBlock;
-    const long long b1 = b0 + kCellsPerBlock < N ? b0 + kCellsPerBlock : N;
+    const long long b0 = (long long)blockIdx.x * span;
+    const long long b1 = b0 + span < N ? b0 + span : N;
     const double rhoB = (double)P.rhoB, phiB = (double)P.phiB, drho = (double)P.drho;
     double sm = 0.0, sp = 0.0;
     for (long long k = b0 + threadIdx.x; k < b1; k += blockDim.x) {
@@ -83,7 +92,9 @@ __global__ void k_mass_noalloc_final(int nblocks, double *__restrict__ scratch) 
 // Device address of g_mass_scratch for the current device.  In host code
 // the name g_mass_scratch is only a host-side stand-in, not a device
 // address, so it is looked up with cudaGetSymbolAddress once per device
-// (with that device current) and cached.
+// (with that device current) and cached.  The cache outlives a
+// cudaDeviceReset, after which the library is not to be used on that
+// device again.
 std::mutex g_scratch_mu;
 double *g_scratch_dev[64] = {};
 
@@ -108,10 +119,10 @@ lbm_status scratch_address(double **out) {
 }
 
 template <class T, class ST>
-cudaError_t launch(const lbm::Derived &d, const void *level, double *scratch, int nblocks,
-                   cudaStream_t s) {
+cudaError_t launch(const lbm::Derived &d, const void *level, double *scratch, long long span,
+                   int nblocks, cudaStream_t s) {
     k_mass_noalloc_partial<T, ST><<<nblocks, 256, 0, s>>>(static_cast<const char *>(level),
-                                                          lbm::make_kp<T>(d), scratch);
+                                                          lbm::make_kp<T>(d), span, scratch);
     k_mass_noalloc_final<<<1, 32, 0, s>>>(nblocks, scratch);
     return cudaGetLastError();
 }
@@ -147,14 +158,17 @@ extern "C" lbm_status lbm_mass_noalloc(const lbm_params *prm, const void *level,
     d.tau_f = prm->tau_f;
     d.tau_g = prm->tau_g;
 
-    const int nblocks = (int)((N + kCellsPerBlock - 1) / kCellsPerBlock);
+    const long long span = block_span(N);
+    const int nblocks = (int)((N + span - 1) / span);  // <= kMaxBlocks for N <= kMaxCells
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     switch (prm->dtype) {
-        case LBM_F64: e = launch<double, lbm::PlainStore<double>>(d, level, scratch, nblocks, s); break;
-        case LBM_F32: e = launch<float, lbm::PlainStore<float>>(d, level, scratch, nblocks, s); break;
-        case LBM_F16S: e = launch<float, lbm::Store16<__half>>(d, level, scratch, nblocks, s); break;
-        default: e = launch<float, lbm::Store16<__nv_bfloat16>>(d, level, scratch, nblocks, s); break;
+        case LBM_F64: e = launch<double, lbm::PlainStore<double>>(d, level, scratch, span, nblocks, s); break;
+        case LBM_F32: e = launch<float, lbm::PlainStore<float>>(d, level, scratch, span, nblocks, s); break;
+        case LBM_F16S: e = launch<float, lbm::Store16<__half>>(d, level, scratch, span, nblocks, s); break;
+        case LBM_BF16S: e = launch<float, lbm::Store16<__nv_bfloat16>>(d, level, scratch, span, nblocks, s); break;
+        case LBM_F16D: e = launch<float, lbm::Store16D<__half>>(d, level, scratch, span, nblocks, s); break;
+        default: e = launch<float, lbm::Store16D<__nv_bfloat16>>(d, level, scratch, span, nblocks, s); break;
     }
     double h[2] = {0.0, 0.0};
     if (e == cudaSuccess)

@@ -6,10 +6,12 @@ buffer, on scratch that lives inside the library.
 
 Checked through the C ABI against lbm_mass, the entry point that uses a
 caller-bound work buffer: the two reduce in different orders, so they agree
-to FP64 rounding (the 1e-12 relative bound of the other mass tests).  Three
+to FP64 rounding (the 1e-12 relative bound of the other mass tests).  Four
 calls in a row, largest grid first, so a later call on a smaller grid would
-expose stale partial sums left by the earlier one.  This file is collected
-last so that a run stopping at the first failure has run every other test.
+expose stale partial sums left by the earlier one; the first grid (1500 x
+1400) spans several reduction blocks with a partial last block, and the
+four calls cover every storage form.  This file is collected last so that
+a run stopping at the first failure has run every other test.
 """
 import ctypes
 
@@ -42,11 +44,12 @@ def _noalloc(L, params, dtype, level_ptr, stream_ptr):
 
 
 def test_noalloc_mass_matches_lbm_mass_on_consecutive_calls(L):
-    p1, phi1 = W.precision(n=1536, n_drops=72)
+    p1, phi1, ux1, uy1 = W.small_case(1500, 1400, seed=22)
     p2, phi2 = W.droplet64()
     p3, phi3, ux3, uy3 = W.small_case(70, 45, seed=21, walls=True, gravity=1e-5, u_wall=0.01)
-    cases = [(p1, phi1, None, None, "f32", 30), (p2, phi2, None, None, "f64", 40),
-             (p3, phi3, ux3, uy3, "f16s", 25)]
+    p4, phi4 = W.precision(n=512, n_drops=8)
+    cases = [(p1, phi1, ux1, uy1, "f32", 30), (p2, phi2, None, None, "f64", 40),
+             (p3, phi3, ux3, uy3, "f16s", 25), (p4, phi4, None, None, "bf16s", 20)]
     for p, phi, ux, uy, dtype, steps in cases:
         sim = L.Sim(p, dtype)
         sim.init_phi(phi, ux, uy)
