@@ -36,7 +36,9 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_CELL = {"f64": 288, "f32": 144, "f16s": 76, "bf16s": 76}
+# populations read once and written once per cell-update; the deviation
+# forms also move their two 16-bit reference words (P, A) each way
+BYTES_PER_CELL = {"f64": 288, "f32": 144, "f16s": 76, "bf16s": 76, "f16d": 84, "bf16d": 84}
 WORKLOAD = "precision-4096x4096-512-droplets-rho100"
 CPU_SAMPLE_N, CPU_SAMPLE_DROPS, CPU_SAMPLE_STEPS = 1024, 32, 20
 
@@ -53,7 +55,7 @@ def _peaks():
 
 # Sources that define the step kernels (k_strip, k_step) and their launch.
 STEP_SOURCES = ("lbm_internal.h", "lbm_kernels.cuh", "lbm_strip.cuh", "lbm_strip_lag.cuh",
-                "lbm_ops.cuh", "lbm_f64.cu", "lbm_f32.cu", "lbm_f16.cu")
+                "lbm_ops.cuh", "lbm_f64.cu", "lbm_f32.cu", "lbm_f16.cu", "lbm_f16d.cu")
 
 
 # Sources of the D3Q19 step kernels and their launch.
@@ -564,7 +566,7 @@ def main():
     if not args.no_forms:
         forms = {}
         ref = None
-        for dtype in ("f64", "f16s", "bf16s"):
+        for dtype in ("f64", "f16s", "bf16s", "f16d", "bf16d"):
             ksteps = args.steps if dtype != "f64" else max(10, args.steps // 10)
             s2, tot, per2, _ = measure(dtype, ksteps, args.warmup)
             m2 = cells * ksteps * world / (tot * 1e-3) / 1e6
@@ -587,16 +589,16 @@ def main():
         s64 = lbm.Sim(p, "f64")
         s64.init_phi(phi)
         s64.step(K)
-        ref = s64.fields(("phi", "ux", "uy"))
+        ref = s64.fields(("phi", "ux", "uy", "p"))
         s64.close()
-        for dtype in ("f32", "f16s", "bf16s"):
+        for dtype in ("f32", "f16s", "bf16s", "f16d", "bf16d"):
             s3 = lbm.Sim(p, dtype)
             s3.init_phi(phi)
             s3.step(K)
-            f3 = s3.fields(("phi", "ux", "uy"))
+            f3 = s3.fields(("phi", "ux", "uy", "p"))
             s3.close()
             errs[dtype] = {k: float((f3[k].double() - ref[k]).abs().max().item()) for k in f3}
-        for dtype in ("f16s", "bf16s"):
+        for dtype in ("f16s", "bf16s", "f16d", "bf16d"):
             forms[dtype]["gain_vs_f32"] = round(forms[dtype]["mlups"] / mlups, 3)
             forms[dtype]["max_abs_err_vs_f64"] = errs[dtype]
             forms[dtype]["steps_for_err"] = K

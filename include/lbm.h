@@ -61,7 +61,16 @@ typedef enum {
     LBM_F64 = 0,  /* populations and arithmetic in FP64 */
     LBM_F32 = 1,  /* populations and arithmetic in FP32 */
     LBM_F16S = 2, /* FP32 arithmetic; f_0..8 and g_1..8 stored as scaled FP16, g_0 in FP32 */
-    LBM_BF16S = 3 /* FP32 arithmetic; f_0..8 and g_1..8 stored as BF16, g_0 in FP32 */
+    LBM_BF16S = 3, /* FP32 arithmetic; f_0..8 and g_1..8 stored as BF16, g_0 in FP32 */
+    /* FP32 arithmetic; f_0..8 and g_1..8 stored as their deviations from the
+     * rest equilibrium of the cell they sit on (Eqs. 24-27 at u = 0:
+     * w_i p and w_i alpha mu, with p and alpha mu of that cell's previous
+     * time level, cut to 16 bits and stored beside the populations), in
+     * scaled FP16 (LBM_F16D) or BF16 (LBM_BF16D); g_0 in FP32.  Single
+     * domains with nx a multiple of 8 only (not batches, slabs, the lagged
+     * variant or the adjoint). */
+    LBM_F16D = 4,
+    LBM_BF16D = 5
 } lbm_dtype;
 
 typedef enum { LBM_PERIODIC = 0, LBM_WALL = 1 } lbm_bc;
@@ -215,6 +224,33 @@ LBM_API lbm_status lbm_adj_step(lbm_sim *sim, const void *state_t, const void *l
 LBM_API lbm_status lbm_adj_init(lbm_sim *sim, const void *phi0, const void *lam_0,
                                 void *phi0_bar, void *work);
 LBM_API lbm_status lbm_adj_grads(lbm_sim *sim, void *work, double *dM, double *dsigma);
+
+/* One checkpoint segment of the reverse sweep in one call: the recompute
+ * of the segment's states and its n reverse steps, the sequence that
+ * checkpoint-and-recompute repeats for every segment.  The step is the one
+ * of Eqs. 22-32 (Sec. 3); the paper itself has no adjoint.
+ *   n             steps in the segment (>= 1), t0 .. t0+n-1
+ *   states        device buffer of n levels, `level_stride` bytes apart
+ *                 (>= lbm_state_bytes, 256-byte aligned, as is `states`):
+ *                 level 0 holds s_{t0} (the checkpoint) on entry; levels
+ *                 1 .. n-1 are overwritten with s_{t0+1} .. s_{t0+n-1},
+ *                 computed by the forward step
+ *   lam           lambda_{t0+n} on entry, lambda_{t0} on return
+ *   lam_tmp       a second lambda buffer (scratch), not lam
+ *   work          the adjoint work buffer; the segment's dL/dM, dL/dsigma
+ *                 contributions are added to its running totals
+ * Same result, bit for bit, as n - 1 calls of lbm_step's kernel followed
+ * by n calls of lbm_adj_step.  Asynchronous on the handle's stream; the
+ * handle's own state and step count are untouched.  With
+ * lbm_adj_set_graph(sim, 1) the launch sequence is captured in a CUDA graph
+ * on the first call and replayed by later calls with the same n, buffers
+ * and stride (a call with others captures again); graph replay needs a
+ * stream other than the default stream.  Errors: as lbm_adj_step, plus
+ * LBM_ERR_ARG for n < 1, lam == lam_tmp, a NULL buffer or a bad stride or
+ * alignment, and for lbm_adj_set_graph(sim, 1) on the default stream. */
+LBM_API lbm_status lbm_adj_segment(lbm_sim *sim, int64_t n, void *states, size_t level_stride,
+                                   void *lam, void *lam_tmp, void *work);
+LBM_API lbm_status lbm_adj_set_graph(lbm_sim *sim, int on);
 
 /* ------------------------------------------------------------------ batches
  * The batched form: n independent domains, each with its own size and
@@ -395,8 +431,9 @@ LBM_API void lbm3_destroy(lbm3_sim *s);
  * invalid parameters or a NULL level, LBM_ERR_NONFINITE for NaN/Inf sums,
  * LBM_ERR_CUDA for a failed CUDA call; lbm_create_error() gives the
  * message.  The first call on each device looks up the scratch array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls in the process share the one scratch array,
+ * device address (cudaGetSymbolAddress) and keeps it for the process; make
+ * that first call before any stream capture, and make no call on a device
+ * after a cudaDeviceReset of it.  All calls in the process share the one scratch array,
  * which keeps the last call's contents (each call writes every slot it
  * reads, so nothing needs clearing): calls that overlap on the GPU, from
  * any thread or stream, race with each other. */

@@ -5,10 +5,12 @@ L = sum_x (phi_T(x) - target(x))^2 after `steps` steps from the
 equilibrium state of phi0 (u = 0), as a torch scalar that supports
 backward() with respect to phi0, M (mobility lambda) and sigma (surface
 tension).  Forward and backward run in the CUDA library: the forward keeps
-a checkpoint every K steps; the backward recomputes each segment of K steps
-from its checkpoint, then applies the hand-written adjoint step
-(lbm_adj_step) K times in reverse, and finally the adjoint of the initial
-state (lbm_adj_init).  Memory: steps/K checkpoints plus K states.
+a checkpoint every K steps; the backward hands each segment of K steps,
+last first, to lbm_adj_segment, which recomputes the segment's states from
+its checkpoint and applies the hand-written adjoint step K times in
+reverse (replayed from a CUDA graph after the first segment of each
+length), and finally the adjoint of the initial state (lbm_adj_init).
+Memory: steps/K checkpoints plus K states.
 """
 from __future__ import annotations
 
@@ -21,17 +23,23 @@ class LBMRollout(torch.autograd.Function):
     @staticmethod
     def forward(ctx, phi0, M, sigma, params, steps, target, K, dtype):
         p = dict(params, M=float(M), sigma=float(sigma))
-        sim = lbm.Sim(p, dtype)
-        sim.init_phi(phi0.detach())
-        ckpt = []
-        for t in range(steps):
-            if t % K == 0:
+        # a stream of its own: the backward replays its segments as CUDA
+        # graphs, which cannot be captured on the default stream
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            sim = lbm.Sim(p, dtype, stream=stream)
+            sim.init_phi(phi0.detach())
+            ckpt = []
+            t = 0
+            while t < steps:
                 ckpt.append(sim.get_state()[0])
-            sim.step(1)
-        state_T, _ = sim.get_state()
-        work = sim.adj_work()
-        lam = torch.empty_like(state_T)
-        loss = sim.adj_seed(state_T, target.detach(), lam, work)
+                n = min(K, steps - t)
+                sim.step(n)
+                t += n
+            state_T, _ = sim.get_state()
+            work = sim.adj_work()
+            lam = torch.empty_like(state_T)
+            loss = sim.adj_seed(state_T, target.detach(), lam, work)
         ctx.sim, ctx.ckpt, ctx.lam, ctx.work = sim, ckpt, lam, work
         ctx.steps, ctx.K = steps, K
         ctx.save_for_backward(phi0.detach())
@@ -41,21 +49,24 @@ class LBMRollout(torch.autograd.Function):
     def backward(ctx, grad_out):
         sim, lam, work = ctx.sim, ctx.lam, ctx.work
         (phi0,) = ctx.saved_tensors
-        other = torch.empty_like(lam)
         steps, K = ctx.steps, ctx.K
-        for seg in reversed(range(len(ctx.ckpt))):
-            t0 = seg * K
-            n = min(K, steps - t0)
-            sim.set_state(ctx.ckpt[seg], t0)
-            states = []
-            for _ in range(n):
-                states.append(sim.get_state()[0])
-                sim.step(1)
-            for k in reversed(range(n)):
-                sim.adj_step(states[k], lam, other, work)
-                lam, other = other, lam
-        phi_bar = sim.adj_init(phi0, lam, work)
-        dM, dS = sim.adj_grads(work)
+        with torch.cuda.stream(sim.stream):
+            sb = sim.state_bytes()
+            stride = (sb + 255) // 256 * 256
+            states = torch.empty(min(K, steps) * stride, dtype=torch.uint8, device=lam.device)
+            other = torch.empty_like(lam)
+            sim.adj_set_graph(True)
+            # one call per segment, last segment first: level 0 of `states`
+            # takes the checkpoint, the library recomputes the rest of the
+            # segment and runs its reverse steps (graph replay after the
+            # first segment of each length)
+            for seg in reversed(range(len(ctx.ckpt))):
+                t0 = seg * K
+                n = min(K, steps - t0)
+                states[:sb].copy_(ctx.ckpt[seg])
+                sim.adj_segment(n, states, stride, lam, other, work)
+            phi_bar = sim.adj_init(phi0, lam, work)
+            dM, dS = sim.adj_grads(work)
         g = float(grad_out)
         sim.close()
         return (phi_bar.to(device=phi0.device, dtype=phi0.dtype) * g,

@@ -17,6 +17,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "liblbm.so")
+# The same sources with LBM_DEBUG defined: every population and field index
+# of the single-domain kernels is bounds-checked; a failed check sets an
+# error word that the next lbm_mass / lbm_laplace returns as LBM_ERR_STATE.
+LIB_DEBUG = os.path.join(HERE, "liblbm_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I" + INCLUDE,
@@ -26,6 +30,7 @@ UNITS = {
     "lbm_f64": ["-fmad=false"],
     "lbm_f32": [],
     "lbm_f16": [],
+    "lbm_f16d": [],
     "lbm_noalloc": [],
     "lbm_batch": [],
     "lbm_slabs": [],
@@ -46,16 +51,20 @@ def _sources_mtime() -> float:
     return max(os.path.getmtime(p) for p in paths)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link liblbm.so if any source is newer than it."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _sources_mtime():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile and link liblbm.so (debug: liblbm_debug.so, with LBM_DEBUG
+    defined) if any source is newer than it."""
+    lib = LIB_DEBUG if debug else LIB
+    bdir = os.path.join(BUILD, "debug") if debug else BUILD
+    extra = ["-DLBM_DEBUG"] if debug else []
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _sources_mtime():
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
 
     def compile_unit(name):
-        obj = os.path.join(BUILD, name + ".o")
-        cmd = [nvcc, *ARCH, *COMMON, *UNITS[name], "-c", os.path.join(CSRC, name + ".cu"),
+        obj = os.path.join(bdir, name + ".o")
+        cmd = [nvcc, *ARCH, *COMMON, *extra, *UNITS[name], "-c", os.path.join(CSRC, name + ".cu"),
                "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -66,14 +75,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
         objs = list(ex.map(compile_unit, UNITS))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, "-o", tmp, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv))

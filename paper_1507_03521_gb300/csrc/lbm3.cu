@@ -262,6 +262,7 @@ lbm_status lbm3_init_phi(lbm3_sim *s, const void *phi, const void *ux, const voi
 
 lbm_status lbm3_step(lbm3_sim *s, int64_t n) {
     if (!s) return LBM_ERR_ARG;
+    lbm::NvtxRange r_call("lbm3_step");
     if (lbm_status st = s->ready()) return st;
     if (!s->initialized) return s->fail(LBM_ERR_STATE, "lbm3_step before lbm3_init_phi");
     if (n < 0) return s->fail(LBM_ERR_ARG, "negative step count");

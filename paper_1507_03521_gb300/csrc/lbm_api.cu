@@ -61,6 +61,8 @@ const Ops *ops_for(int dtype) {
         case LBM_F32: return lbm::ops_f32();
         case LBM_F16S: return lbm::ops_f16s();
         case LBM_BF16S: return lbm::ops_bf16s();
+        case LBM_F16D: return lbm::ops_f16d();
+        case LBM_BF16D: return lbm::ops_bf16d();
         default: return nullptr;
     }
 }
@@ -81,6 +83,10 @@ std::string check_params(const lbm_params *p) {
     if (!ops_for(p->dtype)) return "unknown dtype";
     if (p->gradp_lag != 0 && p->gradp_lag != 1) return "gradp_lag must be 0 or 1";
     if (p->gradp_lag && p->nx % 8 != 0) return "the lagged-grad-p variant needs nx a multiple of 8";
+    if (is_deviation_dtype(p->dtype) && p->nx % 8 != 0)
+        return "the deviation storage (LBM_F16D, LBM_BF16D) needs nx a multiple of 8";
+    if (is_deviation_dtype(p->dtype) && p->gradp_lag)
+        return "the deviation storage takes the synchronous step (gradp_lag = 0)";
     const double vals[] = {p->rho_A, p->rho_B, p->phi_A, p->phi_B, p->sigma, p->W, p->M,
                            p->tau_f, p->tau_g, p->gravity, p->rho_ref, p->u_wall_bottom,
                            p->u_wall_top};
@@ -153,6 +159,17 @@ struct lbm_sim {
     int64_t steps = 0;
     bool initialized = false;
     std::string err;
+    // adjoint segments (lbm_adj_segment): optional CUDA-graph replay of the
+    // launch sequence, kept for the last (n, buffers) it was captured for
+    bool adj_graph = false;
+    cudaGraphExec_t adj_exec = nullptr;
+    int64_t adj_n = -1;
+    size_t adj_stride = 0;
+    const void *adj_key[4] = {nullptr, nullptr, nullptr, nullptr};
+
+    ~lbm_sim() {
+        if (adj_exec) cudaGraphExecDestroy(adj_exec);
+    }
 
     char *level(int i) { return state + (size_t)i * L.level; }
     char *slot(int i) { return work + (size_t)i * L.field_slot; }
@@ -173,6 +190,24 @@ struct lbm_sim {
         return LBM_OK;
     }
 };
+
+// LBM_DEBUG builds: the bounds-check word, read after the stream is
+// synchronised; a set bit is a failed index check (code = bit number).
+static lbm_status debug_word(lbm_sim *s) {
+#ifdef LBM_DEBUG
+    unsigned w = 0;
+    if (cudaMemcpy(&w, s->d.dbg, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return s->fail(LBM_ERR_CUDA, "reading the LBM_DEBUG check word");
+    if (w) return s->fail(LBM_ERR_STATE, "LBM_DEBUG index check failed, codes 0x" + [&] {
+        char b[16];
+        snprintf(b, sizeof(b), "%x", w);
+        return std::string(b);
+    }());
+#else
+    (void)s;
+#endif
+    return LBM_OK;
+}
 
 #define LBM_CK(sim, call)                                   \
     do {                                                    \
@@ -216,9 +251,9 @@ lbm_status lbm_create(const lbm_params *prm, void *stream, lbm_sim **out) {
     s->prm = *prm;
     s->d = derive(prm);
     s->ops = ops_for(prm->dtype);
-    if (s->d.lag && !s->ops->strip_ok(s->d)) {
+    if ((s->d.lag || lbm::is_deviation_dtype(prm->dtype)) && !s->ops->strip_ok(s->d)) {
         delete s;
-        g_create_err = "the lagged-grad-p variant needs the strip form (grid too large)";
+        g_create_err = "this dtype or variant needs the strip form (grid too large)";
         return LBM_ERR_ARG;
     }
     s->L = layout(s->d, s->ops);
@@ -239,11 +274,15 @@ lbm_status lbm_bind_buffers(lbm_sim *s, void *state, size_t state_bytes, void *w
     s->state = static_cast<char *>(state);
     s->work = static_cast<char *>(work);
     s->initialized = false;
+    // the bounds-check word of LBM_DEBUG builds: a spare word of the
+    // reduction output area (release builds never touch it)
+    s->d.dbg = reinterpret_cast<unsigned *>(s->work + s->L.out_off + 128);
     return LBM_OK;
 }
 
 lbm_status lbm_init_phi(lbm_sim *s, const void *phi, const void *ux, const void *uy, int on_host) {
     if (!s) return LBM_ERR_ARG;
+    lbm::NvtxRange r_call("lbm_init_phi");
     if (lbm_status st = s->ready()) return st;
     if (!phi) return s->fail(LBM_ERR_ARG, "phi is null");
     const size_t fb = (size_t)s->d.N * s->ops->field_size;
@@ -261,6 +300,9 @@ lbm_status lbm_init_phi(lbm_sim *s, const void *phi, const void *ux, const void 
         }
     }
     s->cur = 0;
+#ifdef LBM_DEBUG
+    LBM_CK(s, cudaMemsetAsync(s->d.dbg, 0, sizeof(unsigned), s->stream));
+#endif
     LBM_CK(s, s->ops->init(s->d, dphi, dux, duy, s->level(0), s->stream));
     if (s->d.lag)  // the previous-step pressure of the initial state: p = 0
         LBM_CK(s, cudaMemsetAsync(s->level(0) + p_slot_offset(s->d, s->ops), 0,
@@ -273,10 +315,12 @@ lbm_status lbm_init_phi(lbm_sim *s, const void *phi, const void *ux, const void 
 
 lbm_status lbm_step(lbm_sim *s, int64_t n) {
     if (!s) return LBM_ERR_ARG;
+    lbm::NvtxRange r_call("lbm_step");
     if (lbm_status st = s->ready()) return st;
     if (!s->initialized) return s->fail(LBM_ERR_STATE, "lbm_step before lbm_init_phi");
     if (n < 0) return s->fail(LBM_ERR_ARG, "negative step count");
     for (int64_t t = 0; t < n; ++t) {
+        lbm::NvtxRange r_launch(s->ops->step_range);
         LBM_CK(s, s->ops->step(s->d, s->level(s->cur), s->level(1 - s->cur), s->stream));
         s->cur = 1 - s->cur;
         s->steps++;
@@ -287,6 +331,7 @@ lbm_status lbm_step(lbm_sim *s, int64_t n) {
 lbm_status lbm_fields(lbm_sim *s, void *phi, void *rho, void *p, void *ux, void *uy, void *mu,
                       int on_host) {
     if (!s) return LBM_ERR_ARG;
+    lbm::NvtxRange r_call("lbm_fields");
     if (lbm_status st = s->ready()) return st;
     if (!s->initialized) return s->fail(LBM_ERR_STATE, "lbm_fields before lbm_init_phi");
     void *user[6] = {phi, rho, p, ux, uy, mu};
@@ -306,6 +351,7 @@ lbm_status lbm_fields(lbm_sim *s, void *phi, void *rho, void *p, void *ux, void 
 
 lbm_status lbm_mass(lbm_sim *s, double *mass, double *phi_total) {
     if (!s) return LBM_ERR_ARG;
+    lbm::NvtxRange r_call("lbm_mass");
     if (lbm_status st = s->ready()) return st;
     if (!s->initialized) return s->fail(LBM_ERR_STATE, "lbm_mass before lbm_init_phi");
     long long nb = (s->d.N + 255) / 256;
@@ -314,6 +360,7 @@ lbm_status lbm_mass(lbm_sim *s, double *mass, double *phi_total) {
     LBM_CK(s, s->ops->mass(s->d, s->level(s->cur), s->part(), nblocks, s->out(), s->stream));
     LBM_CK(s, cudaMemcpyAsync(h, s->out(), sizeof(h), cudaMemcpyDeviceToHost, s->stream));
     LBM_CK(s, cudaStreamSynchronize(s->stream));
+    if (lbm_status st = debug_word(s)) return st;
     if (mass) *mass = h[0];
     if (phi_total) *phi_total = h[1];
     if (!std::isfinite(h[0]) || !std::isfinite(h[1]))
@@ -323,6 +370,7 @@ lbm_status lbm_mass(lbm_sim *s, double *mass, double *phi_total) {
 
 lbm_status lbm_laplace(lbm_sim *s, double xc, double yc, double R, double *dP, double *R_eff) {
     if (!s) return LBM_ERR_ARG;
+    lbm::NvtxRange r_call("lbm_laplace");
     if (lbm_status st = s->ready()) return st;
     if (!s->initialized) return s->fail(LBM_ERR_STATE, "lbm_laplace before lbm_init_phi");
     LBM_CK(s, s->ops->fields(s->d, s->level(s->cur), s->slot(0), nullptr, nullptr, nullptr,
@@ -335,6 +383,7 @@ lbm_status lbm_laplace(lbm_sim *s, double xc, double yc, double R, double *dP, d
                               s->part(), nblocks, s->out(), s->stream));
     LBM_CK(s, cudaMemcpyAsync(h, s->out(), sizeof(h), cudaMemcpyDeviceToHost, s->stream));
     LBM_CK(s, cudaStreamSynchronize(s->stream));
+    if (lbm_status st = debug_word(s)) return st;
     if (dP) *dP = (h[1] > 0 && h[3] > 0) ? h[0] / h[1] - h[2] / h[3] : NAN;
     if (R_eff) *R_eff = std::sqrt(h[4] / 3.14159265358979323846);
     if (!std::isfinite(h[0]) || !std::isfinite(h[2]) || !std::isfinite(h[4]))
@@ -362,6 +411,9 @@ lbm_status lbm_set_state(lbm_sim *s, const void *src, int on_host, int64_t step)
     if (lbm_status st = s->ready()) return st;
     if (!src) return s->fail(LBM_ERR_ARG, "null source");
     s->cur = 0;
+#ifdef LBM_DEBUG
+    LBM_CK(s, cudaMemsetAsync(s->d.dbg, 0, sizeof(unsigned), s->stream));
+#endif
     LBM_CK(s, cudaMemcpyAsync(s->level(0), src, lbm_state_bytes(s),
                               on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                               s->stream));
@@ -431,6 +483,7 @@ lbm_status lbm_adj_seed(lbm_sim *s, const void *state_T, const void *phi_target,
 
 lbm_status lbm_adj_step(lbm_sim *s, const void *state_t, const void *lam_next, void *lam_t,
                         void *work) {
+    lbm::NvtxRange r_call("lbm_adj_step");
     if (lbm_status st = adj_ready(s, work)) return st;
     if (!state_t || !lam_next || !lam_t) return s->fail(LBM_ERR_ARG, "null pointer");
     if (lam_next == lam_t) return s->fail(LBM_ERR_ARG, "lam_next and lam_t must differ");
@@ -443,6 +496,90 @@ lbm_status lbm_adj_init(lbm_sim *s, const void *phi0, const void *lam_0, void *p
     if (lbm_status st = adj_ready(s, work)) return st;
     if (!phi0 || !lam_0 || !phi0_bar) return s->fail(LBM_ERR_ARG, "null pointer");
     LBM_CK(s, s->ops->adj_init(s->d, adj_host(s->prm), phi0, lam_0, phi0_bar, work, s->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_adj_set_graph(lbm_sim *s, int on) {
+    if (!s) return LBM_ERR_ARG;
+    if (on && (s->stream == nullptr || s->stream == cudaStreamLegacy || s->stream == cudaStreamPerThread))
+        return s->fail(LBM_ERR_ARG, "graph replay needs a stream other than the default stream");
+    s->adj_graph = on != 0;
+    return LBM_OK;
+}
+
+// The launch sequence of one segment: n - 1 forward steps that fill levels
+// 1 .. n-1 of `states` from level 0, then n reverse steps from the last
+// level down, alternating between lam and lam_tmp so that lambda_{t0}
+// lands in lam.
+static cudaError_t adj_segment_issue(lbm_sim *s, int64_t n, char *states, size_t lb, void *lam,
+                                     void *lam_tmp, void *work) {
+    const Ops *o = s->ops;
+    for (int64_t k = 1; k < n; ++k) {
+        cudaError_t e = o->step(s->d, states + (k - 1) * lb, states + k * lb, s->stream);
+        if (e != cudaSuccess) return e;
+    }
+    const size_t sb = level_state_bytes(s->d, o);
+    void *in = lam, *out = lam_tmp;
+    if (n % 2 == 1) {  // an odd count ends in lam only if it starts from lam_tmp
+        cudaError_t e = cudaMemcpyAsync(lam_tmp, lam, sb, cudaMemcpyDeviceToDevice, s->stream);
+        if (e != cudaSuccess) return e;
+        in = lam_tmp;
+        out = lam;
+    }
+    const lbm::AdjHost h = adj_host(s->prm);
+    for (int64_t k = n - 1; k >= 0; --k) {
+        cudaError_t e = o->adj_step(s->d, h, states + k * lb, in, out, work, s->stream);
+        if (e != cudaSuccess) return e;
+        void *t = in;
+        in = out;
+        out = t;
+    }
+    return cudaSuccess;
+}
+
+lbm_status lbm_adj_segment(lbm_sim *s, int64_t n, void *states, size_t level_stride, void *lam,
+                           void *lam_tmp, void *work) {
+    lbm::NvtxRange r_call("lbm_adj_segment");
+    if (lbm_status st = adj_ready(s, work)) return st;
+    if (!states || !lam || !lam_tmp) return s->fail(LBM_ERR_ARG, "null pointer");
+    if (lam == lam_tmp) return s->fail(LBM_ERR_ARG, "lam and lam_tmp must differ");
+    if (n < 1) return s->fail(LBM_ERR_ARG, "a segment needs at least one step");
+    const size_t sb = level_state_bytes(s->d, s->ops);
+    if (level_stride < sb || (level_stride & 255) || (reinterpret_cast<uintptr_t>(states) & 255))
+        return s->fail(LBM_ERR_ARG, "level_stride must be >= lbm_state_bytes and states and "
+                                    "level_stride 256-byte aligned");
+    char *st_base = static_cast<char *>(states);
+    if (!s->adj_graph) {
+        LBM_CK(s, adj_segment_issue(s, n, st_base, level_stride, lam, lam_tmp, work));
+        return LBM_OK;
+    }
+    const void *key[4] = {states, lam, lam_tmp, work};
+    bool same = s->adj_exec && s->adj_n == n && s->adj_stride == level_stride;
+    for (int i = 0; i < 4 && same; ++i) same = s->adj_key[i] == key[i];
+    if (!same) {
+        if (s->adj_exec) {
+            cudaGraphExecDestroy(s->adj_exec);
+            s->adj_exec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        LBM_CK(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t ei = adj_segment_issue(s, n, st_base, level_stride, lam, lam_tmp, work);
+        const cudaError_t ec = cudaStreamEndCapture(s->stream, &g);
+        if (ei != cudaSuccess || ec != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return s->cuda(ei != cudaSuccess ? ei : ec, "capture of an adjoint segment");
+        }
+        const cudaError_t eg = cudaGraphInstantiate(&s->adj_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (eg != cudaSuccess) {
+            s->adj_exec = nullptr;
+            return s->cuda(eg, "instantiation of an adjoint segment graph");
+        }
+        s->adj_n = n;
+        s->adj_stride = level_stride;
+        for (int i = 0; i < 4; ++i) s->adj_key[i] = key[i];
+    }
+    LBM_CK(s, cudaGraphLaunch(s->adj_exec, s->stream));
     return LBM_OK;
 }
 

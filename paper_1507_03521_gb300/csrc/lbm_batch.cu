@@ -47,6 +47,8 @@ std::string make_plan(const lbm_params *prms, int n, Plan &P, const Ops **ops_ou
     if (!prms || n < 1) return "need at least one domain";
     const Ops *ops = ops_for(prms[0].dtype);
     if (!ops) return "unknown dtype";
+    if (lbm::is_deviation_dtype(prms[0].dtype))
+        return "the deviation storage (LBM_F16D, LBM_BF16D) runs single domains only";
     for (int i = 0; i < n; ++i) {
         size_t sb = 0, wb = 0;
         if (lbm_buffer_sizes(&prms[i], &sb, &wb) != LBM_OK)
@@ -193,6 +195,7 @@ lbm_status build_items(lbm_batch *b) {
 // forked stream was measured: no gain over the sequential order.)
 lbm_status launch_step(lbm_batch *b, int parity) {
     const void *doms = b->work + b->P.doms_off;
+    lbm::NvtxRange r_launch("batch step");
     if (b->nitems > 0) {
         int slots = 0;
         LBMB_CK(b, b->ops->batch_slots(&slots));
@@ -328,6 +331,7 @@ lbm_status lbm_batch_set_segment(lbm_batch *b, int seg_h) {
 }
 
 lbm_status lbm_batch_step(lbm_batch *b, int64_t n) {
+    lbm::NvtxRange r_call("lbm_batch_step");
     if (!b) return LBM_ERR_ARG;
     if (!b->initialized) return b->fail(LBM_ERR_STATE, "lbm_batch_step before lbm_batch_init_phi");
     if (n < 0) return b->fail(LBM_ERR_ARG, "negative step count");

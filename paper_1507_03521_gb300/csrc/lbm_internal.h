@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <atomic>
 #include <mutex>
 #include <string>
@@ -12,6 +14,16 @@
 #include "lbm.h"
 
 namespace lbm {
+
+// An NVTX range over a scope (entry points and the launches in them), for
+// profilers that record NVTX (ncu --nvtx, Nsight Systems).  Without an
+// attached tool a push or pop is a no-op call.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // A value set up once per device (kernel attributes, occupancy) and shared
 // by every host thread that launches: the first caller on a device runs
@@ -56,6 +68,9 @@ struct Derived {
     // launches of this domain that run at the same time (the y-slabs of one
     // step): each strip launch sizes its grid for 1/share of the GPU
     int share = 1;
+    // device word that the bounds checks of a LBM_DEBUG build set (null:
+    // unchecked); release builds ignore it
+    unsigned *dbg = nullptr;
     double phiA, phiB, phibar, rhoB, drho;
     double kappa, beta, alpha, lambda, gamma;
     double grav, rhoref, tau_f, tau_g, uwb, uwt;
@@ -121,12 +136,18 @@ struct Ops {
     cudaError_t (*batch_slots_narrow)(int *slots);
     cudaError_t (*batch_step_narrow)(char *state, const void *doms, const BatchItem *items, int nitems,
                                      unsigned long long *tickets, int parity, int grid, cudaStream_t s);
+    // NVTX range name of one step launch ("step <name>")
+    const char *step_range = "step";
 };
 
 const Ops *ops_f64();
 const Ops *ops_f32();
 const Ops *ops_f16s();
 const Ops *ops_bf16s();
+const Ops *ops_f16d();
+const Ops *ops_bf16d();
+// The 16-bit deviation storage (single domains on the strip kernel only).
+inline bool is_deviation_dtype(int dtype) { return dtype == LBM_F16D || dtype == LBM_BF16D; }
 
 // Launchers for an lbm_dtype value (null if unknown).
 const Ops *ops_for(int dtype);

@@ -29,6 +29,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace lbm {
 
@@ -72,7 +73,26 @@ struct KP {
     T grav, rhoref;         // F_b,y = -(rho - rhoref) grav
     T itf, itg, pf, pg;     // 1/tau_f, 1/tau_g, 1 - 1/(2 tau_f), 1 - 1/(2 tau_g)
     T uwb, uwt;             // wall x-velocities (bottom, top)
+#ifdef LBM_DEBUG
+    unsigned *dbg;          // bounds-check error word (LBM_DEBUG builds)
+#endif
 };
+
+// Index checks of the LBM_DEBUG build.  LBM_IDX_OK(P, cond, code) is true
+// in release builds; in a LBM_DEBUG build a false `cond` sets bit `code` of
+// the handle's error word (which the next synchronising call reports as
+// LBM_ERR_STATE) and the caller skips the access.  Codes: 1 population row
+// copied to shared memory, 2 population stored, 3 shared row column read,
+// 4 field-ring column, 5 population loaded by the tile kernel.
+#ifdef LBM_DEBUG
+__device__ __forceinline__ bool dbg_ok(unsigned *w, bool ok, unsigned code) {
+    if (!ok && w) atomicOr(w, 1u << code);
+    return ok;
+}
+#define LBM_IDX_OK(P, cond, code) ::lbm::dbg_ok((P).dbg, (cond), (code))
+#else
+#define LBM_IDX_OK(P, cond, code) true
+#endif
 
 // Output pointers of FIELDS mode (any may be null).
 template <class T>
@@ -221,6 +241,110 @@ struct Store16 {
     }
 };
 
+// 16-bit storage of the deviations from the rest equilibrium, FP32
+// arithmetic.  At rest (u = 0) the equilibria of Eqs. 24-27 are
+//   f_i = w_i p,   g_i = w_i alpha mu (i >= 1),   g_0 = phi - (1 - w_0) alpha mu,
+// so a population that arrives at cell y is stored as its deviation from
+// the rest equilibrium at y's own p and alpha mu of the previous time
+// level: d f_i = f_i - w_i P_y, d g_i = g_i - w_i A_y (i >= 1).  The sender
+// of a population knows its destination's p and mu (they are on chip when
+// it collides), and cell y stores its own P_y and A_y beside its
+// populations, so encoder and decoder use the same references.  P_y and A_y
+// are p and alpha mu cut to their upper 16 bits (a BF16 value rounded
+// toward zero): any value serves as a reference as long as both sides use
+// it, and this one costs one bit operation each way.  g_0 stays in FP32 as
+// phi - sum_{i>0} g_i(decoded), as in Store16.
+// Level layout: g_0 (NS floats), then 19 NS of H: f_0..f_8, g_1..g_8, then
+// the reference words P (slot 17) and A (slot 18).
+template <class H>
+struct Store16D {
+    using C = float;
+    using E = HalfStore<H>;
+    static constexpr bool kDev = true;
+    static size_t level_bytes(long long NS) { return (size_t)NS * (4 + 19 * 2); }
+    static void slot_span(long long NS, int q, size_t *off, size_t *elem) {
+        Store16<H>::slot_span(NS, q, off, elem);
+    }
+    // reference words: the upper half of the FP32 bit pattern
+    __host__ __device__ __forceinline__ static unsigned short ref_word(float v) {
+#ifdef __CUDA_ARCH__
+        return (unsigned short)(__float_as_uint(v) >> 16);
+#else
+        unsigned u;
+        memcpy(&u, &v, 4);
+        return (unsigned short)(u >> 16);
+#endif
+    }
+    __device__ __forceinline__ static float ref_value(unsigned short r) {
+        return __uint_as_float((unsigned)r << 16);
+    }
+    // p or alpha mu cut to its reference value
+    __device__ __forceinline__ static float ref_cut(float v) {
+        return __uint_as_float(__float_as_uint(v) & 0xffff0000u);
+    }
+    // decoded population: stored deviation plus w_i times the reference
+    // (the same rounding at the encoder, which needs the decoded g_i)
+    __device__ __forceinline__ static float rebuild(unsigned short q, float wref) {
+        return __fadd_rn(E::dec(q), wref);
+    }
+    __device__ __forceinline__ static void load(const char *lvl, long long NS, long long k,
+                                                C f[9], C g[9]) {
+        const float *g0 = reinterpret_cast<const float *>(lvl);
+        const unsigned short *h = reinterpret_cast<const unsigned short *>(lvl + NS * 4);
+        const float Pr = ref_value(__ldg(h + 17 * NS + k)), Ar = ref_value(__ldg(h + 18 * NS + k));
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            f[i] = rebuild(__ldg(h + i * NS + k), __fmul_rn(float(D2Q9::w(i)), Pr));
+        g[0] = __ldg(g0 + k);
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+            g[i] = rebuild(__ldg(h + (8 + i) * NS + k), __fmul_rn(float(D2Q9::w(i)), Ar));
+    }
+    __device__ __forceinline__ static C load_phi(const char *lvl, long long NS, long long k) {
+        C f[9], g[9];
+        load(lvl, NS, k, f, g);
+        C s = g[0];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) s += g[i];
+        return s;
+    }
+    // fv/gv: final values per source direction i, written to slot sl[i] of
+    // cell kk[i], whose reference values (already cut) are rP[i], rA[i];
+    // ownP, ownA: this cell's p and alpha mu (its own reference words).
+    __device__ __forceinline__ static void store(char *lvl, long long NS, const int sl[9],
+                                                 const long long kk[9], const C fv[9],
+                                                 const C gv[9], C phi, const float rP[9],
+                                                 const float rA[9], float ownP, float ownA) {
+        float *g0 = reinterpret_cast<float *>(lvl);
+        unsigned short *h = reinterpret_cast<unsigned short *>(lvl + NS * 4);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float wP = __fmul_rn(float(D2Q9::w(i)), rP[i]);
+            h[sl[i] * NS + kk[i]] = E::enc(__fsub_rn(fv[i], wP));
+        }
+        float rest = phi;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const float wA = __fmul_rn(float(D2Q9::w(i)), rA[i]);
+            const unsigned short q = E::enc(__fsub_rn(gv[i], wA));
+            rest -= rebuild(q, wA);
+            h[(8 + sl[i]) * NS + kk[i]] = q;
+        }
+        g0[kk[0]] = rest;  // slot 0 never moves and never bounces
+        h[17 * NS + kk[0]] = ref_word(ownP);
+        h[18 * NS + kk[0]] = ref_word(ownA);
+    }
+};
+
+template <class ST>
+struct IsDev {
+    static constexpr bool value = false;
+};
+template <class H>
+struct IsDev<Store16D<H>> {
+    static constexpr bool value = true;
+};
+
 // ------------------------------------------------------------ helpers
 
 __device__ __forceinline__ int wrap_x(int x, int nx) {
@@ -348,6 +472,7 @@ k_step(const char *__restrict__ src, char *__restrict__ dst, const KP<T> P, Fiel
     for (int r = 0; r < RPT; ++r) {
         const int ly = ty + 8 * r, lx = tx;
         const long long k = (long long)src_row(y0 + ly, ny, wall) * nx + wrap_x(x0 + lx, nx);
+        if (!LBM_IDX_OK(P, k >= 0 && k < (long long)nx * ny, 5)) continue;
         ST::load(src, NS, k, fr[r], gr[r]);
         T phi, ps, jx, jy;
         moments(fr[r], gr[r], phi, ps, jx, jy);
@@ -364,6 +489,7 @@ k_step(const char *__restrict__ src, char *__restrict__ dst, const KP<T> P, Fiel
         if (ly >= 0 && ly < TY && lx >= 0 && lx < TL::TX) continue;
         const bool ring1 = (ly >= -1 && ly <= TY && lx >= -1 && lx <= TL::TX);
         const long long k = (long long)src_row(y0 + ly, ny, wall) * nx + wrap_x(x0 + lx, nx);
+        if (!LBM_IDX_OK(P, k >= 0 && k < (long long)nx * ny, 5)) continue;
         if (ring1) {
             T f[9], g[9], phi, ps, jx, jy;
             ST::load(src, NS, k, f, g);
@@ -496,7 +622,11 @@ k_step(const char *__restrict__ src, char *__restrict__ dst, const KP<T> P, Fiel
             fv[i] = fs;
             gv[i] = gs;
         }
-        ST::store(dst, NS, sl, kk, fv, gv, phi);
+        bool in = true;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) in = in && kk[i] >= 0 && kk[i] < (long long)nx * ny;
+        if constexpr (!IsDev<ST>::value)
+            if (LBM_IDX_OK(P, in, 2)) ST::store(dst, NS, sl, kk, fv, gv, phi);
     }
 }
 
@@ -544,7 +674,20 @@ k_init(const T *__restrict__ phi0, const T *__restrict__ ux0, const T *__restric
             sl[i] = i;
             kk[i] = k;
         }
-        ST::store(lvl, P.NS, sl, kk, fv, gv, ph);
+        if constexpr (IsDev<ST>::value) {
+            // every population sits on its own cell: its references are
+            // the cell's own p (0) and alpha mu, cut
+            float rP[9], rA[9];
+            const float A = ST::ref_cut(float(amu));
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                rP[i] = 0.0f;
+                rA[i] = A;
+            }
+            ST::store(lvl, P.NS, sl, kk, fv, gv, ph, rP, rA, 0.0f, float(amu));
+        } else {
+            ST::store(lvl, P.NS, sl, kk, fv, gv, ph);
+        }
     }
 }
 

@@ -42,6 +42,9 @@ inline KP<T> make_kp(const Derived &d) {
     k.pg = T(1.0 - 0.5 / d.tau_g);
     k.uwb = T(d.uwb);
     k.uwt = T(d.uwt);
+#ifdef LBM_DEBUG
+    k.dbg = d.dbg;
+#endif
     return k;
 }
 
@@ -97,8 +100,17 @@ struct OpsImpl {
         return cudaSuccess;
     }
 
+    // The deviation storage (Store16D) runs single domains on the strip
+    // kernel only: no tile-kernel step, slabs, batches or lagged variant.
+    static constexpr bool kDev = IsDev<ST>::value;
+
     template <bool SLAB>
     static cudaError_t strip_step(const Derived &d, const void *src, void *dst, cudaStream_t s) {
+        if constexpr (kDev && SLAB) return cudaErrorNotSupported;
+        else return strip_step_impl<SLAB>(d, src, dst, s);
+    }
+    template <bool SLAB>
+    static cudaError_t strip_step_impl(const Derived &d, const void *src, void *dst, cudaStream_t s) {
         dim3 grid;
         int seg_h = 0;
         cudaError_t e = strip_grid<SLAB>(d, grid, seg_h);
@@ -113,6 +125,10 @@ struct OpsImpl {
     using LS = LagSmem<T, ST, SW, DEPTH>;
     static size_t p_offset(long long NS) { return (ST::level_bytes(NS) + 255) & ~size_t(255); }
     static cudaError_t lag_step(const Derived &d, const void *src, void *dst, cudaStream_t s) {
+        if constexpr (kDev) return cudaErrorNotSupported;
+        else return lag_step_impl(d, src, dst, s);
+    }
+    static cudaError_t lag_step_impl(const Derived &d, const void *src, void *dst, cudaStream_t s) {
         static PerDevice<StripCfg> cfg;
         StripCfg c;
         cudaError_t e = cfg.get(c, [](int dev, StripCfg &v) {
@@ -152,6 +168,14 @@ struct OpsImpl {
     static cudaError_t step(const Derived &d, const void *src, void *dst, cudaStream_t s) {
         // a y-slab (lbm_slabs.cu) and the lagged variant have been checked
         // for the strip form
+        if constexpr (kDev) {
+            if (d.lag || d.slab || !strip_ok(d)) return cudaErrorNotSupported;
+            return strip_step<false>(d, src, dst, s);
+        } else {
+            return step_any(d, src, dst, s);
+        }
+    }
+    static cudaError_t step_any(const Derived &d, const void *src, void *dst, cudaStream_t s) {
         if (d.lag) return strip_ok(d) ? lag_step(d, src, dst, s) : cudaErrorInvalidValue;
         if (d.slab) return strip_ok(d) ? strip_step<true>(d, src, dst, s) : cudaErrorInvalidValue;
         if (strip_ok(d)) return strip_step<false>(d, src, dst, s);
@@ -215,6 +239,10 @@ struct OpsImpl {
     }
 
     static cudaError_t batch_slots(int *slots) {
+        if constexpr (kDev) return cudaErrorNotSupported;
+        else return batch_slots_impl(slots);
+    }
+    static cudaError_t batch_slots_impl(int *slots) {
         static PerDevice<StripCfg> cfg;
         StripCfg c;
         cudaError_t e = cfg.get(c, [](int dev, StripCfg &v) {
@@ -227,8 +255,14 @@ struct OpsImpl {
 
     static cudaError_t batch_step(char *state, const void *doms, const BatchItem *items, int nitems,
                                   unsigned long long *tickets, int parity, int grid, cudaStream_t s) {
+        if constexpr (kDev) return cudaErrorNotSupported;
+        else return batch_step_impl(state, doms, items, nitems, tickets, parity, grid, s);
+    }
+    static cudaError_t batch_step_impl(char *state, const void *doms, const BatchItem *items,
+                                       int nitems, unsigned long long *tickets, int parity, int grid,
+                                       cudaStream_t s) {
         int slots = 0;
-        cudaError_t e = batch_slots(&slots);  // also sets the shared-memory attribute
+        cudaError_t e = batch_slots_impl(&slots);  // also sets the shared-memory attribute
         if (e != cudaSuccess) return e;
         k_strip_batch<T, ST, SW, DEPTH><<<grid, NT, SM::bytes, s>>>(
             state, static_cast<const BatchDom<T> *>(doms), items, nitems, tickets, parity);
@@ -282,7 +316,9 @@ struct OpsImpl {
         k_adj_f1<T><<<nb, 256, 0, s>>>(P, W);
         k_adj_f2<T><<<nb, 256, 0, s>>>(P, W);
         k_adj_f3<T><<<nb, 256, 0, s>>>(P, W);
-        k_adj_collide<T><<<nb, 256, 0, s>>>(static_cast<const T *>(lam_next), L, P, W);
+        // one wave of the collision adjoint (3 CTAs of 256 per SM)
+        const int nbc = nb < kAdjBlocks * 3 / 4 ? nb : kAdjBlocks * 3 / 4;
+        k_adj_collide<T><<<nbc, 256, 0, s>>>(static_cast<const T *>(lam_next), L, P, W);
         k_adj_p<T><<<nb, 256, 0, s>>>(L, P, W);
         k_adj_mu<T><<<nb, 256, 0, s>>>(P, W, part(d, work));  // also the (M, sigma) partials
         k_adj_phi<T><<<nb, 256, 0, s>>>(L, P, W);
@@ -317,6 +353,8 @@ struct OpsImpl {
               &B::batch_fill_dom,       &B::batch_slots,   &B::batch_step,
               kPlain ? &adj_seed : nullptr, kPlain ? &adj_step : nullptr,
               kPlain ? &adj_init : nullptr, 0, nullptr, nullptr};
+        static const std::string range = std::string("step ") + name;
+        o.step_range = range.c_str();
         if constexpr (!std::is_same<BN, void>::value) {
             o.narrow_width = BN::kSW;
             o.batch_slots_narrow = &BN::batch_slots;

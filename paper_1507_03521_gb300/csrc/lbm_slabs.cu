@@ -73,6 +73,8 @@ std::string make_plan(const lbm_params *p, int n, const int *starts, Plan &P, co
     std::string m = lbm::check_params(p);
     if (!m.empty()) return m;
     if (p->gradp_lag) return "slabs take the synchronous step (gradp_lag = 0)";
+    if (lbm::is_deviation_dtype(p->dtype))
+        return "the deviation storage (LBM_F16D, LBM_BF16D) runs single domains only";
     const Ops *ops = lbm::ops_for(p->dtype);
     P.d = lbm::derive(p);
     if (n < 1) return "need at least one slab";
@@ -361,6 +363,7 @@ lbm_status lbm_slabs_gather(lbm_slabs *s, void *level, int64_t *step) {
 
 lbm_status lbm_slabs_step(lbm_slabs *s, int64_t n) {
     if (!s) return LBM_ERR_ARG;
+    lbm::NvtxRange r_call("lbm_slabs_step");
     if (!s->initialized) return s->fail(LBM_ERR_STATE, "lbm_slabs_step before lbm_slabs_scatter");
     if (n < 0) return s->fail(LBM_ERR_ARG, "negative step count");
     for (int64_t t = 0; t < n; ++t) {
@@ -374,6 +377,7 @@ lbm_status lbm_slabs_step(lbm_slabs *s, int64_t n) {
             for (cudaStream_t t : s->side)
                 if (lbm_status st = s->cuda(cudaStreamWaitEvent(t, s->fork, 0), "fork")) return st;
         }
+        lbm::NvtxRange r_launch(s->ops->step_range);
         for (int i = 0; i < s->n(); ++i)
             if (lbm_status st = s->cuda(s->ops->step(s->P.ds[i], s->level(i, s->cur), s->level(i, nxt),
                                                      i == 0 || !par ? s->stream : s->side[i - 1]),

@@ -253,6 +253,131 @@ struct StripRow<Store16<H>, SW> {
     }
 };
 
+// Deviation storage: an f row carries f_0..f_8 and the reference word P
+// (10 half slots), a g row g_0 (floats), g_1..g_8 and the reference word A
+// (9 half slots).  Reads rebuild the populations from the references of
+// the row's own cells; pushes take the references of the destination
+// cells (rP, rA, already cut) and write this cell's own words.
+template <class H, int SW>
+struct StripRow<Store16D<H>, SW> {
+    using C = float;
+    using ST = Store16D<H>;
+    using E = HalfStore<H>;
+    static constexpr int HP = 8;
+    static constexpr int LW = SW + 2 * HP;
+    static constexpr int CH = LW / 8, C0 = LW / 4;
+    static constexpr int TF = 10 * CH;         // f row: f_0..f_8, P
+    static constexpr int TG = C0 + 9 * CH;     // g row: g_0 floats, g_1..g_8, A
+    static constexpr int NT = strip_threads(SW);
+    static constexpr int NF = (TF + NT - 1) / NT, NG = (TG + NT - 1) / NT;
+    static constexpr size_t fbytes = (size_t)10 * LW * 2;
+    static constexpr size_t gbytes = (size_t)LW * 4 + (size_t)9 * LW * 2;
+    static bool idx32_ok(long long NS) { return 21 * NS < (1LL << 31); }
+
+    struct Desc {
+        int foff[NF], fso[NF];
+        int goff[NG], gso[NG];
+        unsigned gflt;
+    };
+    // global half slot of f row slot sl (0..9) and of g row half slot sl (0..8)
+    __device__ __forceinline__ static int fslot(int sl) { return sl < 9 ? sl : 17; }
+    __device__ __forceinline__ static int gslot(int sl) { return sl < 8 ? 9 + sl : 18; }
+    __device__ __forceinline__ static void describe(Desc &d, int t, long long NS, int x_start,
+                                                    int nx, int need) {
+        const int ns = (int)NS;
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            const int j = t + k * NT;
+            if (j < TF && (j % CH) * 8 < need) {
+                const int sl = j / CH, c = j - sl * CH;
+                d.foff[k] = (2 + fslot(sl)) * ns + wrap_any(x_start + c * 8, nx);
+                d.fso[k] = sl * LW + c * 8;
+            } else {
+                d.foff[k] = -1;
+                d.fso[k] = 0;
+            }
+        }
+        d.gflt = 0;
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+            const int j = t + k * NT;
+            if (j < C0 && j * 4 < need) {
+                d.goff[k] = wrap_any(x_start + j * 4, nx);
+                d.gso[k] = j * 16;
+                d.gflt |= 1u << k;
+            } else if (j >= C0 && j < TG && ((j - C0) % CH) * 8 < need) {
+                const int jj = j - C0;
+                const int sl = jj / CH, c = jj - sl * CH;
+                d.goff[k] = (2 + gslot(sl)) * ns + wrap_any(x_start + c * 8, nx);
+                d.gso[k] = LW * 4 + (sl * LW + c * 8) * 2;
+            } else {
+                d.goff[k] = -1;
+                d.gso[k] = 0;
+            }
+        }
+    }
+    __device__ __forceinline__ static void issue_f(const Desc &d, char *sbuf, const char *lvl,
+                                                   int rowbase) {
+        const unsigned short *h = reinterpret_cast<const unsigned short *>(lvl);
+        unsigned short *sh = reinterpret_cast<unsigned short *>(sbuf);
+#pragma unroll
+        for (int k = 0; k < NF; ++k)
+            if (d.foff[k] >= 0) cp_async16(sh + d.fso[k], h + (d.foff[k] + rowbase));
+    }
+    __device__ __forceinline__ static void issue_g(const Desc &d, char *sbuf, const char *lvl,
+                                                   int rowbase) {
+        const float *g0 = reinterpret_cast<const float *>(lvl);
+        const unsigned short *h = reinterpret_cast<const unsigned short *>(lvl);
+#pragma unroll
+        for (int k = 0; k < NG; ++k) {
+            if (d.goff[k] < 0) continue;
+            const void *src = ((d.gflt >> k) & 1u) ? static_cast<const void *>(g0 + (d.goff[k] + rowbase))
+                                                   : static_cast<const void *>(h + (d.goff[k] + rowbase));
+            cp_async16(sbuf + d.gso[k], src);
+        }
+    }
+    __device__ __forceinline__ static void read_f(const char *fbuf, int c, C f[9]) {
+        const unsigned short *sh = reinterpret_cast<const unsigned short *>(fbuf);
+        const float Pr = ST::ref_value(sh[9 * LW + c]);
+        const float w0 = __fmul_rn(float(D2Q9::w(0)), Pr), w1 = __fmul_rn(float(D2Q9::w(1)), Pr),
+                    w5 = __fmul_rn(float(D2Q9::w(5)), Pr);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = ST::rebuild(sh[i * LW + c], i == 0 ? w0 : (i < 5 ? w1 : w5));
+    }
+    __device__ __forceinline__ static void read_g(const char *gbuf, int c, C g[9]) {
+        const float *s0 = reinterpret_cast<const float *>(gbuf);
+        const unsigned short *sh = reinterpret_cast<const unsigned short *>(gbuf + (size_t)LW * 4);
+        const float Ar = ST::ref_value(sh[8 * LW + c]);
+        const float w1 = __fmul_rn(float(D2Q9::w(1)), Ar), w5 = __fmul_rn(float(D2Q9::w(5)), Ar);
+        g[0] = s0[c];
+#pragma unroll
+        for (int i = 1; i < 9; ++i) g[i] = ST::rebuild(sh[(i - 1) * LW + c], i < 5 ? w1 : w5);
+    }
+    __device__ __forceinline__ static void store_fast(char *lvl, int NS, int nx, int kb,
+                                                      const C fv[9], const C gv[9], C phi,
+                                                      const float rP[9], const float rA[9],
+                                                      float ownP, float ownA) {
+        float *g0 = reinterpret_cast<float *>(lvl);
+        unsigned short *h = reinterpret_cast<unsigned short *>(lvl + (size_t)NS * 4) + kb;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float wP = __fmul_rn(float(D2Q9::w(i)), rP[i]);
+            h[i * NS + D2Q9::cy(i) * nx + D2Q9::cx(i)] = E::enc(__fsub_rn(fv[i], wP));
+        }
+        float rest = phi;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            const float wA = __fmul_rn(float(D2Q9::w(i)), rA[i]);
+            const unsigned short q = E::enc(__fsub_rn(gv[i], wA));
+            rest -= ST::rebuild(q, wA);
+            h[(8 + i) * NS + D2Q9::cy(i) * nx + D2Q9::cx(i)] = q;
+        }
+        g0[kb] = rest;
+        h[17 * NS] = ST::ref_word(ownP);
+        h[18 * NS] = ST::ref_word(ownA);
+    }
+};
+
 // Shared-memory layout of one strip CTA.
 template <class T, class ST, int SW, int DEPTH>
 struct StripSmem {
@@ -272,8 +397,11 @@ struct StripSmem {
         std::is_same<ST, PlainStore<float>>::value && strip_threads(SW) != SW;
     static constexpr int NBG = DEPTH + 4, NBF = FCARRY ? DEPTH + 1 : DEPTH + 2;
     static constexpr int F1 = FCARRY ? 0 : 1;
-    // rows live at iteration y: phi y..y+3, mu y..y+2, p y-1..y+1
-    static constexpr int RPHI = 4, RMU = 3, RP = 3;
+    // rows live at iteration y: phi y..y+3, mu y..y+2 (and y-1 with the
+    // deviation storage, whose pushes need the destinations' mu), p
+    // y-1..y+1; mu[MU0 + k] holds row y+k
+    static constexpr bool DEV = IsDev<ST>::value;
+    static constexpr int RPHI = 4, RMU = DEV ? 4 : 3, RP = 3, MU0 = RMU - 3;
     static constexpr int WPHI = SW + 6, WMU = SW + 4, WQ = SW + 2;
     static constexpr size_t gb = (SR::gbytes + 15) / 16 * 16;
     static constexpr size_t fb = (SR::fbytes + 15) / 16 * 16;
@@ -514,10 +642,17 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     // DEPTH iterations earlier, as one commit group.  The collisions of the
     // segment need p from row ys-1 on, so the f rows of the first warm-up
     // iterations are not loaded (the p they would give is never used).
+    const int lvl_rows = SLAB ? P.rows : ny;  // rows a level holds
     auto issue_for = [&](int it, int gslot, int fslot) {
         const int gr = it + 3, fr = it + 1;
-        if (gr <= ye + 2) SR::issue_g(desc, at(gslot), src, buf_row<SLAB>(P, gr) * nx);
-        if (fr >= ys - 1 && fr <= ye) SR::issue_f(desc, at(fslot), src, buf_row<SLAB>(P, fr) * nx);
+        if (gr <= ye + 2) {
+            const int b = buf_row<SLAB>(P, gr);
+            if (LBM_IDX_OK(P, b >= 0 && b < lvl_rows, 1)) SR::issue_g(desc, at(gslot), src, b * nx);
+        }
+        if (fr >= ys - 1 && fr <= ye) {
+            const int b = buf_row<SLAB>(P, fr);
+            if (LBM_IDX_OK(P, b >= 0 && b < lvl_rows, 1)) SR::issue_f(desc, at(fslot), src, b * nx);
+        }
         cp_async_commit();  // one group per iteration, possibly empty
     };
 #pragma unroll
@@ -543,6 +678,7 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
             const char *b = at(R.g[3]);
             T *ph = atT(R.ph[3]);
             columns<SW, 3, 3>(t, [&](int c) {
+                if (!LBM_IDX_OK(P, c >= -3 && c < SW + 3 && c + HP >= 0 && c + HP < SR::LW, 3)) return;
                 T g[9];
                 SR::read_g(b, c + HP, g);
                 ph[c] = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
@@ -553,12 +689,13 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
         // 3. mu at row y+2, columns -2 .. SW+1 (Eq. 5)
         {
             const int r = y + 2;
-            T *mo = atT(R.mu[2]);
+            T *mo = atT(R.mu[SM::MU0 + 2]);
             const bool ghost = wall && (r < 0 || r >= ny);
             if (!ghost) {
                 const T *pu = atT(R.ph[3]), *pc = atT(R.ph[2]), *pd = atT(R.ph[1]);
-                T *mlow = (wall && r == 0) ? atT(R.mu[1]) : nullptr;  // row -1
+                T *mlow = (wall && r == 0) ? atT(R.mu[SM::MU0 + 1]) : nullptr;  // row -1
                 columns<SW, 2, 1>(t, [&](int c) {
+                    if (!LBM_IDX_OK(P, c >= -2 && c < SW + 2, 4)) return;
                     const T C = pc[c];
                     // lap = (2/cs2) sum w_i (phi(x + c_i) - phi(x)), differences first
                     const T ax = ((pc[c + 1] - C) + (pc[c - 1] - C)) + ((pu[c] - C) + (pd[c] - C));
@@ -569,7 +706,7 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
                     if (mlow) mlow[c] = m;  // ghost row -1 mirrors row 0
                 });
             } else if (r == ny) {
-                const T *mm = atT(R.mu[1]);  // mirror row ny-1 (already computed)
+                const T *mm = atT(R.mu[SM::MU0 + 1]);  // mirror row ny-1 (already computed)
                 columns<SW, 2, 1>(t, [&](int c) { mo[c] = mm[c]; });
             }
             // r < 0 at a wall: row -1 is written when row 0 is computed;
@@ -586,9 +723,11 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
             T *po = atT(R.p[2]);
             if (!wall || (r >= 0 && r < ny)) {
                 const T *pu = atT(R.ph[2]), *pc = atT(R.ph[1]), *pd = atT(R.ph[0]);
-                const T *mu_ = atT(R.mu[2]), *mc = atT(R.mu[1]), *md = atT(R.mu[0]);
+                const T *mu_ = atT(R.mu[SM::MU0 + 2]), *mc = atT(R.mu[SM::MU0 + 1]),
+                        *md = atT(R.mu[SM::MU0]);
                 const char *fbr = at(R.f[SM::F1]);
                 auto point = [&](int c, bool keep) {
+                    if (!LBM_IDX_OK(P, c >= -1 && c < SW + 1 && c + HP >= 0 && c + HP < SR::LW, 3)) return;
                     T f[9];
                     SR::read_f(fbr, c + HP, f);
                     const T sf = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
@@ -662,7 +801,7 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
                 const T gpy = T(1.0 / 3.0) * (pu[c] - pd0) +
                               T(1.0 / 12.0) * ((pu[c + 1] + pu[c - 1]) - (pdm + pdp));
                 const T phi = atT(R.ph[0])[c];
-                const T mu = atT(R.mu[0])[c];
+                const T mu = atT(R.mu[SM::MU0])[c];
                 const T pv = pc[c];
                 const T rho = P.rhoB + (phi - P.phiB) * P.drho;
                 T f[9], g[9];
@@ -681,8 +820,29 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
                 // across its edges land in its ghost rows)
                 const bool y_inner = (y > 0 && y < ny - 1) || (SLAB && !wall);
                 const int yl = SLAB ? y - P.y0 : y;  // row within the level
-                if (x_inner && y_inner) {
-                    SR::store_fast(dst, NS, nx, yl * nx + gx, fv, gv, phi);
+                // deviation storage: the references of the destination
+                // cells, p and alpha mu of rows y-1 .. y+1 (cut)
+                float rP[9], rA[9];
+                if constexpr (SM::DEV) {
+                    const T *mrow[3] = {atT(R.mu[SM::MU0 - 1]), atT(R.mu[SM::MU0]),
+                                        atT(R.mu[SM::MU0 + 1])};
+                    const T *prow[3] = {pd, pc, pu};
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const int cx = D2Q9::cx(i), cy = D2Q9::cy(i);
+                        rP[i] = ST::ref_cut(prow[cy + 1][c + cx]);
+                        rA[i] = ST::ref_cut(P.alpha * mrow[cy + 1][c + cx]);
+                    }
+                }
+                // every push lands inside the level: the farthest are
+                // kb - nx - 1 and kb + nx + 1 on the fast path
+                if (x_inner && y_inner &&
+                    LBM_IDX_OK(P, (yl - 1) * nx + gx - 1 >= 0 && (yl + 1) * nx + gx + 1 < lvl_rows * nx, 2)) {
+                    if constexpr (SM::DEV)
+                        SR::store_fast(dst, NS, nx, yl * nx + gx, fv, gv, phi, rP, rA, pv,
+                                       P.alpha * mu);
+                    else
+                        SR::store_fast(dst, NS, nx, yl * nx + gx, fv, gv, phi);
                 } else {
                     int sl[9];
                     long long kk[9];
@@ -698,6 +858,10 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
                             gv[i] -= T(6) * w * phi * cuw;
                             sl[i] = D2Q9::opp(i);
                             kk[i] = k;
+                            if constexpr (SM::DEV) {  // bounced back: this cell's references
+                                rP[i] = rP[0];
+                                rA[i] = rA[0];
+                            }
                         } else {
                             int xd = gx + cx;
                             xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
@@ -707,7 +871,15 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
                             kk[i] = (long long)yy * nx + xd;
                         }
                     }
-                    ST::store(dst, P.NS, sl, kk, fv, gv, phi);
+                    bool in = true;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i)
+                        in = in && kk[i] >= 0 && kk[i] < (long long)lvl_rows * nx && sl[i] >= 0 && sl[i] < 9;
+                    if (!LBM_IDX_OK(P, in, 2)) {
+                    } else if constexpr (SM::DEV)
+                        ST::store(dst, P.NS, sl, kk, fv, gv, phi, rP, rA, pv, P.alpha * mu);
+                    else
+                        ST::store(dst, P.NS, sl, kk, fv, gv, phi);
                 }
             }
         }

@@ -16,9 +16,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblbm.so")
 
-F64, F32, F16S, BF16S = 0, 1, 2, 3
+F64, F32, F16S, BF16S, F16D, BF16D = 0, 1, 2, 3, 4, 5
 PERIODIC, WALL = 0, 1
-DTYPES = {"f64": F64, "f32": F32, "f16s": F16S, "bf16s": BF16S}
+DTYPES = {"f64": F64, "f32": F32, "f16s": F16S, "bf16s": BF16S, "f16d": F16D, "bf16d": BF16D}
 
 STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_NONFINITE",
           -4: "LBM_ERR_TIMEOUT", -5: "LBM_ERR_STATE", -6: "LBM_ERR_NOMEM"}
@@ -33,7 +33,7 @@ EXPORTS = ["lbm_version", "lbm_buffer_sizes", "lbm_create", "lbm_bind_buffers", 
            "lbm_batch_autotune", "lbm_batch_fields", "lbm_batch_mass", "lbm_batch_cells",
            "lbm_batch_step_count", "lbm_batch_segment", "lbm_batch_work_items", "lbm_batch_last_error",
            "lbm_batch_destroy", "lbm_adj_work_bytes", "lbm_adj_reset", "lbm_adj_seed",
-           "lbm_adj_step", "lbm_adj_init", "lbm_adj_grads",
+           "lbm_adj_step", "lbm_adj_init", "lbm_adj_grads", "lbm_adj_segment", "lbm_adj_set_graph",
            "lbm_slabs_buffer_sizes", "lbm_slabs_create", "lbm_slabs_bind_buffers",
            "lbm_slabs_scatter", "lbm_slabs_gather", "lbm_slabs_step", "lbm_slabs_rows",
            "lbm_slabs_step_count", "lbm_slabs_last_error", "lbm_slabs_destroy",
@@ -65,8 +65,10 @@ class CParams(ctypes.Structure):
 
 
 _lib = None
+_lib_debug = None
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
+LIB_DEBUG_PATH = os.path.join(HERE, "liblbm_debug.so")
 
 
 def load(path: str = LIB_PATH):
@@ -74,6 +76,20 @@ def load(path: str = LIB_PATH):
     global _lib
     if _lib is not None:
         return _lib
+    _lib = _open(path)
+    return _lib
+
+
+def load_debug():
+    """Load liblbm_debug.so, the LBM_DEBUG build (bounds-checked indices),
+    built by build.build(debug=True)."""
+    global _lib_debug
+    if _lib_debug is None:
+        _lib_debug = _open(LIB_DEBUG_PATH)
+    return _lib_debug
+
+
+def _open(path: str):
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: build it with "
                            "`python -c 'import __graft_entry__ as g; g.build()'`")
@@ -205,7 +221,10 @@ def load(path: str = LIB_PATH):
     lib.lbm_adj_init.argtypes = [_vp, _vp, _vp, _vp, _vp]
     lib.lbm_adj_grads.restype = S
     lib.lbm_adj_grads.argtypes = [_vp, _vp, _dp, _dp]
-    _lib = lib
+    lib.lbm_adj_segment.restype = S
+    lib.lbm_adj_segment.argtypes = [_vp, ctypes.c_int64, _vp, ctypes.c_size_t, _vp, _vp, _vp]
+    lib.lbm_adj_set_graph.restype = S
+    lib.lbm_adj_set_graph.argtypes = [_vp, ctypes.c_int]
     return lib
 
 
@@ -242,16 +261,17 @@ class Sim:
     """One domain on the current CUDA device.
 
     ``params`` is a dict in the paper's notation (see workloads.py);
-    ``dtype`` one of "f64", "f32", "f16s", "bf16s".  Buffers are torch
-    tensors owned by this object; the stream is torch's current stream at
-    construction unless one is given.
+    ``dtype`` one of "f64", "f32", "f16s", "bf16s", "f16d", "bf16d".
+    Buffers are torch tensors owned by this object; the stream is torch's
+    current stream at construction unless one is given.  ``debug`` runs the
+    handle on liblbm_debug.so, the bounds-checked LBM_DEBUG build.
     """
 
-    def __init__(self, params: dict, dtype="f32", stream=None, device=None):
+    def __init__(self, params: dict, dtype="f32", stream=None, device=None, debug=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("liblbm needs a CUDA device; none is available")
-        self._lib = load()
+        self._lib = load_debug() if debug else load()
         self.params = dict(params)
         self.dtype = dtype if isinstance(dtype, str) else {v: k for k, v in DTYPES.items()}[dtype]
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -390,6 +410,16 @@ class Sim:
         self._check(self._lib.lbm_adj_init(self._h, ph.data_ptr(), lam0.data_ptr(),
                                            out.data_ptr(), work.data_ptr()))
         return out
+
+    def adj_segment(self, n, states, level_stride, lam, lam_tmp, work):
+        """n reverse steps of one checkpoint segment (lbm_adj_segment):
+        states[0] holds the checkpoint; lam goes from lambda_{t0+n} to
+        lambda_{t0}."""
+        self._check(self._lib.lbm_adj_segment(self._h, int(n), states.data_ptr(), int(level_stride),
+                                              lam.data_ptr(), lam_tmp.data_ptr(), work.data_ptr()))
+
+    def adj_set_graph(self, on: bool):
+        self._check(self._lib.lbm_adj_set_graph(self._h, int(bool(on))))
 
     def adj_grads(self, work):
         dM, dS = ctypes.c_double(), ctypes.c_double()

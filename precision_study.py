@@ -41,7 +41,7 @@ def main():
     n_drops = 512 if args.n == 4096 else max(1, int(512 * (args.n / 4096) ** 2))
     p, phi = W.precision(n=args.n, n_drops=n_drops)
     p = dict(p, rho_B=p["rho_A"] / args.rho_ratio)
-    forms = ("f64", "f32", "f16s", "bf16s")
+    forms = ("f64", "f32", "f16s", "bf16s", "f16d", "bf16d")
     sims = {}
     m0 = {}
     for f in forms:

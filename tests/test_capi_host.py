@@ -36,6 +36,19 @@ def test_exports_match_header(lib):
         assert hasattr(lib, name)
 
 
+def test_debug_build_exports_the_same_entry_points():
+    """liblbm_debug.so (LBM_DEBUG: bounds-checked indices) builds from the
+    same sources and exports exactly the same entry points."""
+    from paper_1507_03521_gb300 import build, lbm
+    path = build.build(debug=True)
+    assert path == lbm.LIB_DEBUG_PATH
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                         check=True).stdout
+    assert {l.split()[-1] for l in out.splitlines() if " T " in l} == _declared()
+    dl = lbm.load_debug()
+    assert dl is not lbm.load() and dl.lbm_version() == 1
+
+
 def test_params_layout_matches_header(tmp_path):
     from paper_1507_03521_gb300 import lbm
     src = tmp_path / "off.c"
@@ -65,8 +78,10 @@ def test_version_and_sizes(lib):
     sb32, wb32 = lbm.buffer_sizes(_params(), "f32")
     sb64, wb64 = lbm.buffer_sizes(_params(), "f64")
     sb16, _ = lbm.buffer_sizes(_params(), "f16s")
+    sb16d, _ = lbm.buffer_sizes(_params(), "f16d")
     N = 64 * 64
     assert sb32 == 2 * 18 * 4 * N and sb64 == 2 * 18 * 8 * N
+    assert sb16d == 2 * (4 + 19 * 2) * N  # 17 deviations and the two reference words
     assert sb16 == 2 * (4 + 17 * 2) * N
     assert sb32 % 256 == 0 and wb32 % 256 == 0 and wb64 > wb32
 

@@ -165,3 +165,63 @@ def test_f32_adjoint_close_to_f64(L):
     assert np.abs(g32[0] - g64[0]).max() <= 1e-3 * np.abs(g64[0]).max()
     assert g32[1] == pytest.approx(g64[1], rel=1e-3)
     assert g32[2] == pytest.approx(g64[2], rel=1e-3)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("graph", [False, True])
+def test_segment_call_equals_step_by_step(L, dtype, graph):
+    """lbm_adj_segment (recompute of a segment from its checkpoint plus its
+    reverse steps, in one call, optionally replayed from a CUDA graph)
+    gives bit for bit the lambda and (M, sigma) totals of recomputing the
+    states with lbm_step and applying lbm_adj_step one step at a time, for
+    odd and even segment lengths and for repeated calls (graph replay)."""
+    p, phi, ux, uy = W.small_case(48, 37, seed=33, walls=True, gravity=1e-5, u_wall=0.01)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        a = L.Sim(p, dtype, stream=stream)
+        a.init_phi(phi, ux, uy)
+        a.step(3)
+        ckpt, _ = a.get_state()
+        sb = a.state_bytes()
+        stride = (sb + 255) // 256 * 256
+        rng = np.random.default_rng(9)
+        elem = 8 if dtype == "f64" else 4
+        lam0 = torch.from_numpy(rng.standard_normal(sb // elem).astype(
+            np.float64 if dtype == "f64" else np.float32)).view(torch.uint8).to(ckpt.device)
+        # reference: one call per reverse step, states from lbm_step
+        ref_lam, ref_g = [], []
+        w_ref = a.adj_work()
+        lam = lam0.clone()
+        other = torch.empty_like(lam)
+        for n in (5, 4, 5):
+            a.set_state(ckpt, 3)
+            states = []
+            for _ in range(n):
+                states.append(a.get_state()[0])
+                a.step(1)
+            for k in reversed(range(n)):
+                a.adj_step(states[k], lam, other, w_ref)
+                lam, other = other, lam
+            ref_lam.append(lam.clone())
+            ref_g.append(a.adj_grads(w_ref))
+        # the segment call, three calls in a row (odd, even, odd length)
+        b = L.Sim(p, dtype, stream=stream)
+        b.init_phi(phi, ux, uy)
+        b.adj_set_graph(graph)
+        w = b.adj_work()
+        states = torch.empty(5 * stride, dtype=torch.uint8, device=ckpt.device)
+        lam = lam0.clone()
+        tmp = torch.empty_like(lam)
+        N = p["nx"] * p["ny"]
+        npdt = np.float64 if dtype == "f64" else np.float32
+
+        def cells(t):  # the 18 slots' cell entries (the padding past N is not lambda)
+            return _state_pops(t, N, npdt)
+
+        for i, n in enumerate((5, 4, 5)):
+            states[:sb].copy_(ckpt)
+            b.adj_segment(n, states, stride, lam, tmp, w)
+            assert np.array_equal(cells(lam), cells(ref_lam[i])), (i, n)
+            assert b.adj_grads(w) == ref_g[i], (i, n)
+        a.close()
+        b.close()
