@@ -187,6 +187,16 @@ LBM_API const char *lbm_create_error(void);
 /* Free the handle's host state.  Bound buffers stay the caller's. */
 LBM_API void lbm_destroy(lbm_sim *sim);
 
+/* Test hook of the timeout path; the paper has no counterpart.  FP32
+ * single domains stage population rows by TMA tile loads, and every wait
+ * for one is bounded (about one second).  With on != 0 the tile loads of
+ * the following steps announce 16 bytes more than they bring, so their
+ * waits run out: the kernel sets the handle's error word and its CTAs
+ * return, and the next lbm_mass or lbm_laplace returns LBM_ERR_TIMEOUT.
+ * The state is then not a valid time level (re-initialise it).  on = 0
+ * restores normal loads.  Errors: LBM_ERR_ARG for a NULL handle. */
+LBM_API lbm_status lbm_test_unfinished_tiles(lbm_sim *sim, int on);
+
 /* ------------------------------------------------------------------ adjoint
  * Hand-written discrete adjoint (vector-Jacobian product) of the step, for
  * LBM_F64 and LBM_F32 handles.  With s_t the populations after t steps
@@ -254,15 +264,19 @@ LBM_API lbm_status lbm_adj_set_graph(lbm_sim *sim, int on);
 
 /* ------------------------------------------------------------------ batches
  * The batched form: n independent domains, each with its own size and
- * parameters (one dtype for the whole batch; every nx a multiple of 8),
- * advanced together by one persistent kernel launch per strip width per
- * time step.  A launch works through a list of (domain, strip, row
- * segment) items sorted by decreasing cost, its CTAs claiming items from a
- * counter in the work buffer: 128-column strips, and (f32, f16s, bf16s) a
- * second list of the strips with at most 64 active columns, stepped at 64
- * columns.  Per-domain results are bit-identical to stepping each domain
- * alone with lbm_step.  Fields and phi are concatenated in domain order,
- * each domain row-major [ny][nx] in the field type.
+ * parameters (one dtype for the whole batch; every nx a multiple of 8; not
+ * the deviation storage), advanced together by one persistent kernel
+ * launch per time step.  The launch works through one list of (domain,
+ * strip, row segment) items, its CTAs claiming items from a counter in the
+ * work buffer: 128-column strips (FP64: 64-column), the strips with more
+ * than 64 active columns first, each group by decreasing cost.  A batch
+ * whose strips all have at most 64 active columns (f32, f16s, bf16s) runs
+ * a kernel of 64-column CTAs instead.  Per-domain results equal (bit for
+ * bit in FP64 and the 16-bit forms; to FP32 rounding in FP32, where each
+ * kernel may contract multiply-adds differently) those of
+ * stepping each domain alone with lbm_step.  Fields and phi are
+ * concatenated in domain order, each domain row-major [ny][nx] in the
+ * field type.
  */
 typedef struct lbm_batch lbm_batch; /* opaque handle, owned by the caller */
 
@@ -328,7 +342,10 @@ LBM_API void lbm_batch_destroy(lbm_batch *b);
  *      owns their row,
  *   3. one copy launch refreshing every ghost row (all 18 slots).
  * Every cell runs the same kernel body as lbm_step, so the gathered state
- * is bit-identical to stepping the whole domain.  Requirements: nx a
+ * equals stepping the whole domain: bit for bit in FP64 and the 16-bit
+ * forms, to FP32 rounding in FP32 (the slab kernel and the whole-domain
+ * kernel are compiled separately and may contract multiply-adds
+ * differently).  Requirements: nx a
  * multiple of 8; every slab >= 3 rows.  `row_starts` (n entries, the first
  * 0, increasing) gives a_i; NULL splits ny evenly.  States are levels in
  * the layout of lbm_get_state for the whole domain (device memory).

@@ -256,8 +256,8 @@ __global__ void k_adj_f3(const AdjP<T> P, AdjW<T> W) {
 // lambda_t (partial: the direct (1 - 1/tau) terms; k_adj_p and k_adj_phi
 // add the terms through p, j and phi).
 template <class T>
-__global__ void __launch_bounds__(256, 3)
-k_adj_collide(const T *__restrict__ lam_next, T *__restrict__ lam, const AdjP<T> P, AdjW<T> W) {
+__global__ void k_adj_collide(const T *__restrict__ lam_next, T *__restrict__ lam, const AdjP<T> P,
+                              AdjW<T> W) {
     const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
     const long long N = (long long)P.k.nx * P.k.ny, NS = P.k.NS;
     const KP<T> &K = P.k;
@@ -372,7 +372,7 @@ k_adj_collide(const T *__restrict__ lam_next, T *__restrict__ lam, const AdjP<T>
 // grad p transposed (extrapolated ghosts) gives the full adjoint of p; then
 // p, u, F backwards (Eqs. 31-32) and the f terms through sum f and j.
 template <class T>
-__global__ void __launch_bounds__(256, 4) k_adj_p(T *__restrict__ lam, const AdjP<T> P, AdjW<T> W) {
+__global__ void k_adj_p(T *__restrict__ lam, const AdjP<T> P, AdjW<T> W) {
     const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
     const long long N = (long long)P.k.nx * P.k.ny, NS = P.k.NS;
     const KP<T> &K = P.k;

@@ -4,6 +4,8 @@
 // solved for kappa and beta, Eq. 13, Eq. 17, Eq. 33), buffer layout, and
 // the launch sequence of each entry point.  Every step of the method runs
 // in the kernels of lbm_kernels.cuh.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -191,6 +193,48 @@ struct lbm_sim {
     }
 };
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null if the driver does not provide it.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// The 3-D tensor map (x, row, slot) of one FP32 level for the tensor-tile
+// staging: box = `box` columns x 1 row x 9 slots (one f or g row), no
+// swizzle, zero fill outside (never read: only strips whose rows lie inside
+// the level use the map).  False when the map cannot be made; the strip
+// kernel then copies by chunks.
+static bool encode_level_map(CUtensorMap *m, const void *lvl, const Derived &d, int box) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || box <= 0 || box > 256) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, 18};
+    cuuint64_t strides[2] = {(cuuint64_t)d.nx * 4, (cuuint64_t)d.NS * 4};
+    cuuint32_t boxd[3] = {(cuuint32_t)box, 1, 9};
+    cuuint32_t estr[3] = {1, 1, 1};
+    if ((strides[0] | strides[1]) & 15) return false;
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(lvl), dims, strides, boxd, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The kernels' error word: bit 0, a bounded wait for a tile load ran out.
+static lbm_status error_word(lbm_sim *s) {
+    unsigned w = 0;
+    if (cudaMemcpy(&w, s->d.err, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return s->fail(LBM_ERR_CUDA, "reading the kernels' error word");
+    if (w & 1u) return s->fail(LBM_ERR_TIMEOUT, "a bounded wait for a tile load ran out");
+    return LBM_OK;
+}
+
 // LBM_DEBUG builds: the bounds-check word, read after the stream is
 // synchronised; a set bit is a failed index check (code = bit number).
 static lbm_status debug_word(lbm_sim *s) {
@@ -274,9 +318,16 @@ lbm_status lbm_bind_buffers(lbm_sim *s, void *state, size_t state_bytes, void *w
     s->state = static_cast<char *>(state);
     s->work = static_cast<char *>(work);
     s->initialized = false;
-    // the bounds-check word of LBM_DEBUG builds: a spare word of the
-    // reduction output area (release builds never touch it)
+    // the bounds-check word of LBM_DEBUG builds and the kernels' error
+    // word: spare words of the reduction output area
     s->d.dbg = reinterpret_cast<unsigned *>(s->work + s->L.out_off + 128);
+    s->d.err = reinterpret_cast<unsigned *>(s->work + s->L.out_off + 132);
+    // tensor maps of the two levels for the tensor-tile staging
+    s->d.tm_base[0] = s->d.tm_base[1] = nullptr;
+    if (s->ops->tma_box > 0 && !s->d.lag && s->ops->strip_ok(s->d))
+        for (int i = 0; i < 2; ++i)
+            if (encode_level_map(&s->d.tm[i], s->level(i), s->d, s->ops->tma_box))
+                s->d.tm_base[i] = s->level(i);
     return LBM_OK;
 }
 
@@ -300,9 +351,7 @@ lbm_status lbm_init_phi(lbm_sim *s, const void *phi, const void *ux, const void 
         }
     }
     s->cur = 0;
-#ifdef LBM_DEBUG
-    LBM_CK(s, cudaMemsetAsync(s->d.dbg, 0, sizeof(unsigned), s->stream));
-#endif
+    LBM_CK(s, cudaMemsetAsync(s->d.dbg, 0, 2 * sizeof(unsigned), s->stream));  // dbg, err
     LBM_CK(s, s->ops->init(s->d, dphi, dux, duy, s->level(0), s->stream));
     if (s->d.lag)  // the previous-step pressure of the initial state: p = 0
         LBM_CK(s, cudaMemsetAsync(s->level(0) + p_slot_offset(s->d, s->ops), 0,
@@ -360,6 +409,7 @@ lbm_status lbm_mass(lbm_sim *s, double *mass, double *phi_total) {
     LBM_CK(s, s->ops->mass(s->d, s->level(s->cur), s->part(), nblocks, s->out(), s->stream));
     LBM_CK(s, cudaMemcpyAsync(h, s->out(), sizeof(h), cudaMemcpyDeviceToHost, s->stream));
     LBM_CK(s, cudaStreamSynchronize(s->stream));
+    if (lbm_status st = error_word(s)) return st;
     if (lbm_status st = debug_word(s)) return st;
     if (mass) *mass = h[0];
     if (phi_total) *phi_total = h[1];
@@ -383,6 +433,7 @@ lbm_status lbm_laplace(lbm_sim *s, double xc, double yc, double R, double *dP, d
                               s->part(), nblocks, s->out(), s->stream));
     LBM_CK(s, cudaMemcpyAsync(h, s->out(), sizeof(h), cudaMemcpyDeviceToHost, s->stream));
     LBM_CK(s, cudaStreamSynchronize(s->stream));
+    if (lbm_status st = error_word(s)) return st;
     if (lbm_status st = debug_word(s)) return st;
     if (dP) *dP = (h[1] > 0 && h[3] > 0) ? h[0] / h[1] - h[2] / h[3] : NAN;
     if (R_eff) *R_eff = std::sqrt(h[4] / 3.14159265358979323846);
@@ -411,9 +462,7 @@ lbm_status lbm_set_state(lbm_sim *s, const void *src, int on_host, int64_t step)
     if (lbm_status st = s->ready()) return st;
     if (!src) return s->fail(LBM_ERR_ARG, "null source");
     s->cur = 0;
-#ifdef LBM_DEBUG
-    LBM_CK(s, cudaMemsetAsync(s->d.dbg, 0, sizeof(unsigned), s->stream));
-#endif
+    LBM_CK(s, cudaMemsetAsync(s->d.dbg, 0, 2 * sizeof(unsigned), s->stream));  // dbg, err
     LBM_CK(s, cudaMemcpyAsync(s->level(0), src, lbm_state_bytes(s),
                               on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                               s->stream));
@@ -499,6 +548,12 @@ lbm_status lbm_adj_init(lbm_sim *s, const void *phi0, const void *lam_0, void *p
     return LBM_OK;
 }
 
+lbm_status lbm_test_unfinished_tiles(lbm_sim *s, int on) {
+    if (!s) return LBM_ERR_ARG;
+    s->d.tx_extra = on ? 16u : 0u;
+    return LBM_OK;
+}
+
 lbm_status lbm_adj_set_graph(lbm_sim *s, int on) {
     if (!s) return LBM_ERR_ARG;
     if (on && (s->stream == nullptr || s->stream == cudaStreamLegacy || s->stream == cudaStreamPerThread))
@@ -514,8 +569,15 @@ lbm_status lbm_adj_set_graph(lbm_sim *s, int on) {
 static cudaError_t adj_segment_issue(lbm_sim *s, int64_t n, char *states, size_t lb, void *lam,
                                      void *lam_tmp, void *work) {
     const Ops *o = s->ops;
+    // The recompute runs the kernel lbm_step runs: where the handle's
+    // levels have tensor maps (FP32), each source level of the segment gets
+    // one too.
+    Derived dk = s->d;
     for (int64_t k = 1; k < n; ++k) {
-        cudaError_t e = o->step(s->d, states + (k - 1) * lb, states + k * lb, s->stream);
+        char *src = states + (k - 1) * lb;
+        dk.tm_base[0] = dk.tm_base[1] = nullptr;
+        if (s->d.tm_base[0] && encode_level_map(&dk.tm[0], src, dk, o->tma_box)) dk.tm_base[0] = src;
+        cudaError_t e = o->step(dk, src, states + k * lb, s->stream);
         if (e != cudaSuccess) return e;
     }
     const size_t sb = level_state_bytes(s->d, o);

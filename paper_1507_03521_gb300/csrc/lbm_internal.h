@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <cuda.h>  // CUtensorMap (type only; encoded through the runtime's driver entry point)
 #include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
@@ -71,6 +72,21 @@ struct Derived {
     // device word that the bounds checks of a LBM_DEBUG build set (null:
     // unchecked); release builds ignore it
     unsigned *dbg = nullptr;
+    // device error word of the kernels' bounded waits (null: not reported)
+    unsigned *err = nullptr;
+    // test hook (lbm_test_unfinished_tiles): bytes each tile load announces
+    // beyond what it brings, so that its wait runs out; 0 in normal use
+    unsigned tx_extra = 0;
+    // 3-D tensor maps (x, row, slot) of the handle's two levels, for the
+    // tensor-tile staging of FP32 single domains; tm_base[i] is the level
+    // map i describes (null: none)
+    const void *tm_base[2] = {nullptr, nullptr};
+    CUtensorMap tm[2];
+    const CUtensorMap *map_for(const void *lvl) const {
+        for (int i = 0; i < 2; ++i)
+            if (tm_base[i] && tm_base[i] == lvl) return &tm[i];
+        return nullptr;
+    }
     double phiA, phiB, phibar, rhoB, drho;
     double kappa, beta, alpha, lambda, gamma;
     double grav, rhoref, tau_f, tau_g, uwb, uwt;
@@ -138,6 +154,9 @@ struct Ops {
                                      unsigned long long *tickets, int parity, int grid, cudaStream_t s);
     // NVTX range name of one step launch ("step <name>")
     const char *step_range = "step";
+    // width (x extent) of the tensor-map box of the tensor-tile staging, 0
+    // where the form does not use it
+    int tma_box = 0;
 };
 
 const Ops *ops_f64();

@@ -73,6 +73,8 @@ struct KP {
     T grav, rhoref;         // F_b,y = -(rho - rhoref) grav
     T itf, itg, pf, pg;     // 1/tau_f, 1/tau_g, 1 - 1/(2 tau_f), 1 - 1/(2 tau_g)
     T uwb, uwt;             // wall x-velocities (bottom, top)
+    unsigned *err;          // error word: bit 0 set when a bounded wait ran out (may be null)
+    unsigned tx_extra;      // test hook: bytes a tile load announces beyond what it brings (0)
 #ifdef LBM_DEBUG
     unsigned *dbg;          // bounds-check error word (LBM_DEBUG builds)
 #endif

@@ -42,6 +42,8 @@ inline KP<T> make_kp(const Derived &d) {
     k.pg = T(1.0 - 0.5 / d.tau_g);
     k.uwb = T(d.uwb);
     k.uwt = T(d.uwt);
+    k.err = d.err;
+    k.tx_extra = d.tx_extra;
 #ifdef LBM_DEBUG
     k.dbg = d.dbg;
 #endif
@@ -87,6 +89,11 @@ struct OpsImpl {
             return strip_cfg(k_strip<T, ST, SW, DEPTH, SLAB>, (int)SM::bytes, dev, v);
         });
         if (e != cudaSuccess) return e;
+        one_wave(d, c, grid, seg_h);
+        return cudaSuccess;
+    }
+    // strips x segments ~= the resident CTAs c allows, segments >= 16 rows
+    static void one_wave(const Derived &d, const StripCfg &c, dim3 &grid, int &seg_h) {
         const int strips = (d.nx + SW - 1) / SW;
         const int rows = d.yb - d.ya;  // rows stepped
         long long slots = (long long)c.per_sm * c.sms / (d.share > 1 ? d.share : 1);
@@ -97,7 +104,6 @@ struct OpsImpl {
         seg_h = (int)((rows + nseg - 1) / nseg);
         nseg = (rows + seg_h - 1) / seg_h;
         grid = dim3((unsigned)strips, (unsigned)nseg);
-        return cudaSuccess;
     }
 
     // The deviation storage (Store16D) runs single domains on the strip
@@ -109,14 +115,37 @@ struct OpsImpl {
         if constexpr (kDev && SLAB) return cudaErrorNotSupported;
         else return strip_step_impl<SLAB>(d, src, dst, s);
     }
+    // tensor-tile staging: FP32 single domains whose rows are 128-byte
+    // aligned row buffers (the 120-column strips)
+    static constexpr bool kTma = std::is_same<ST, PlainStore<float>>::value && SM::TMA_ROWS;
+
     template <bool SLAB>
     static cudaError_t strip_step_impl(const Derived &d, const void *src, void *dst, cudaStream_t s) {
+        if constexpr (kTma && !SLAB) {
+            if (const CUtensorMap *m = d.map_for(src)) return strip_step_tma(d, src, dst, *m, s);
+        }
         dim3 grid;
         int seg_h = 0;
         cudaError_t e = strip_grid<SLAB>(d, grid, seg_h);
         if (e != cudaSuccess) return e;
         k_strip<T, ST, SW, DEPTH, SLAB><<<grid, NT, SM::bytes, s>>>(
             static_cast<const char *>(src), static_cast<char *>(dst), make_kp<T>(d), seg_h);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t strip_step_tma(const Derived &d, const void *src, void *dst,
+                                      const CUtensorMap &m, cudaStream_t s) {
+        static PerDevice<StripCfg> cfg;
+        StripCfg c;
+        cudaError_t e = cfg.get(c, [](int dev, StripCfg &v) {
+            return strip_cfg(k_strip_tma<T, ST, SW, DEPTH>, (int)SM::bytes_tma, dev, v);
+        });
+        if (e != cudaSuccess) return e;
+        dim3 grid;
+        int seg_h = 0;
+        one_wave(d, c, grid, seg_h);
+        k_strip_tma<T, ST, SW, DEPTH><<<grid, NT, SM::bytes_tma, s>>>(
+            static_cast<const char *>(src), static_cast<char *>(dst), make_kp<T>(d), seg_h, m);
         return cudaGetLastError();
     }
 
@@ -316,9 +345,7 @@ struct OpsImpl {
         k_adj_f1<T><<<nb, 256, 0, s>>>(P, W);
         k_adj_f2<T><<<nb, 256, 0, s>>>(P, W);
         k_adj_f3<T><<<nb, 256, 0, s>>>(P, W);
-        // one wave of the collision adjoint (3 CTAs of 256 per SM)
-        const int nbc = nb < kAdjBlocks * 3 / 4 ? nb : kAdjBlocks * 3 / 4;
-        k_adj_collide<T><<<nbc, 256, 0, s>>>(static_cast<const T *>(lam_next), L, P, W);
+        k_adj_collide<T><<<nb, 256, 0, s>>>(static_cast<const T *>(lam_next), L, P, W);
         k_adj_p<T><<<nb, 256, 0, s>>>(L, P, W);
         k_adj_mu<T><<<nb, 256, 0, s>>>(P, W, part(d, work));  // also the (M, sigma) partials
         k_adj_phi<T><<<nb, 256, 0, s>>>(L, P, W);
@@ -355,6 +382,7 @@ struct OpsImpl {
               kPlain ? &adj_init : nullptr, 0, nullptr, nullptr};
         static const std::string range = std::string("step ") + name;
         o.step_range = range.c_str();
+        o.tma_box = kTma ? SM::LW : 0;
         if constexpr (!std::is_same<BN, void>::value) {
             o.narrow_width = BN::kSW;
             o.batch_slots_narrow = &BN::batch_slots;

@@ -24,6 +24,8 @@
 //     extrapolated from the two rows inside (same rules as k_step).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the type only; maps are encoded on the host)
+
 #include <type_traits>
 
 #include "lbm_internal.h"
@@ -41,6 +43,65 @@ __device__ __forceinline__ void cp_async_commit() {
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Tensor-tile staging (FP32 single domains, strips that do not wrap in x):
+// one thread copies a whole population row (9 slots x 1 row x LW columns,
+// one box of the level's 3-D tensor map) into shared memory with a TMA
+// load that completes on the ring slot's mbarrier; every thread waits on
+// that barrier's phase before reading the row.
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// one arrival that also announces `bytes` of transfer still to land
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of parity `parity` to complete: false when it
+// has not after about one second (the device's global nanosecond timer),
+// or after kMbarTries polls at most, so that no kernel waits forever on a
+// copy that never lands.
+constexpr int kMbarTries = 1 << 24;
+constexpr unsigned long long kMbarWaitNs = 1000000000ULL;
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (int i = 0; i < kMbarTries; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255) == 255 && global_ns() - t0 > kMbarWaitNs) return false;
+    }
+    return false;
+}
+// 3-D tile load: box at (x, y, z) of the map into shared memory at dst.
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *map, unsigned bar, int x,
+                                            int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];\n" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
+        : "memory");
 }
 
 __device__ __forceinline__ int wrap_any(int x, int nx) {
@@ -416,6 +477,12 @@ struct StripSmem {
     // compiler is held to, so that registers do not become the tighter
     // limit; otherwise (0) the compiler's own choice stands.
     static constexpr int MINB = FCARRY ? int(233472 / (bytes + 1024)) : 0;
+    // tensor-tile staging: one mbarrier per ring slot (g slots, then f
+    // slots) after the rings; the row buffers of a TMA load must start on
+    // 128-byte boundaries, and so must the rows
+    static constexpr size_t bar_off = (bytes + 7) / 8 * 8;
+    static constexpr size_t bytes_tma = bar_off + 8 * (size_t)(NBG + NBF);
+    static constexpr bool TMA_ROWS = gb % 128 == 0 && fb % 128 == 0;
 };
 
 // The ring slots of the rows live at iteration y, as byte offsets into the
@@ -617,10 +684,14 @@ __device__ __forceinline__ void collide(const KP<float> &P, const CellState<floa
 // One work item of the strip form: columns x0 .. x0+SW-1 (clipped to nx),
 // rows ys .. ye-1 of one domain, read from level `src`, written to `dst`.
 // The leading barrier also separates consecutive items of one CTA.
-template <class T, class ST, int SW, int DEPTH, bool SLAB = false>
+// TMA (tensor-tile staging, FP32 single domains): `map` is the source
+// level's 3-D tensor map (x, row, slot); strips whose rows do not wrap in x
+// take their population rows from it, the others copy by 16-byte chunks.
+template <class T, class ST, int SW, int DEPTH, bool SLAB = false, bool TMA = false>
 __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *__restrict__ dst,
                                            const KP<T> &P, const int x0, const int ys,
-                                           const int ye, char *smem_raw) {
+                                           const int ye, char *smem_raw,
+                                           const CUtensorMap *map = nullptr) {
     using SM = StripSmem<T, ST, SW, DEPTH>;
     using SR = typename SM::SR;
     constexpr int HP = SM::HP;
@@ -632,11 +703,33 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     typename SR::Desc desc;
     const int active = nx - x0 < SW ? nx - x0 : SW;
     SR::describe(desc, t, P.NS, x0 - HP, nx, active + 2 * HP);
+    // the rows of this strip lie inside the level without wrapping: tiles
+    const bool tma = TMA && x0 - HP >= 0 && x0 - HP + SR::LW <= nx;
+    unsigned bars = 0;
+    if constexpr (TMA) {
+        static_assert(SM::TMA_ROWS, "TMA rows need 128-byte aligned row buffers");
+        bars = smem_u32(smem_raw + SM::bar_off);
+        if (tma && t == 0) {
+            for (int k = 0; k < SM::NBG + SM::NBF; ++k) mbar_init(bars + 8 * k, 1);
+            mbar_init_fence();
+        }
+    }
     __syncthreads();
 
     RingSlots<SM> R;
     auto at = [&](int off) { return smem_raw + off; };
     auto atT = [&](int off) { return reinterpret_cast<T *>(smem_raw + off); };
+    // barrier of the g slot at byte offset o, of the f slot at o
+    auto gbar = [&](int o) { return bars + 8u * (unsigned)(o / (int)SM::gb); };
+    auto fbar = [&](int o) {
+        return bars + 8u * (unsigned)(SM::NBG + (o - (int)(SM::gb * SM::NBG)) / (int)SM::fb);
+    };
+    // Phase parities follow from the iteration: a g slot is filled and
+    // consumed once every NBG iterations from yfirst on, an f slot once
+    // every NBF iterations from ys - 2 on (the first f row a segment loads
+    // is read at iteration ys - 2).
+    auto gpar = [&](int it) { return (unsigned)((it - yfirst) / SM::NBG) & 1u; };
+    auto fpar = [&](int it) { return (unsigned)((it - (ys - 2)) / SM::NBF) & 1u; };
 
     // Iteration y reads g row y+3 and f row y+1 first; both are issued
     // DEPTH iterations earlier, as one commit group.  The collisions of the
@@ -645,6 +738,23 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     const int lvl_rows = SLAB ? P.rows : ny;  // rows a level holds
     auto issue_for = [&](int it, int gslot, int fslot) {
         const int gr = it + 3, fr = it + 1;
+        if (tma) {
+            if (gr <= ye + 2) {
+                const int b = buf_row<SLAB>(P, gr);
+                if (t == 0 && LBM_IDX_OK(P, b >= 0 && b < lvl_rows, 1)) {
+                    mbar_expect_tx(gbar(gslot), (unsigned)(9 * SR::LW * sizeof(T)) + P.tx_extra);
+                    tma_load_3d(smem_u32(at(gslot)), map, gbar(gslot), x0 - HP, b, 9);
+                }
+            }
+            if (fr >= ys - 1 && fr <= ye) {
+                const int b = buf_row<SLAB>(P, fr);
+                if (t == 0 && LBM_IDX_OK(P, b >= 0 && b < lvl_rows, 1)) {
+                    mbar_expect_tx(fbar(fslot), (unsigned)(9 * SR::LW * sizeof(T)) + P.tx_extra);
+                    tma_load_3d(smem_u32(at(fslot)), map, fbar(fslot), x0 - HP, b, 0);
+                }
+            }
+            return;
+        }
         if (gr <= ye + 2) {
             const int b = buf_row<SLAB>(P, gr);
             if (LBM_IDX_OK(P, b >= 0 && b < lvl_rows, 1)) SR::issue_g(desc, at(gslot), src, b * nx);
@@ -655,8 +765,19 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
         }
         cp_async_commit();  // one group per iteration, possibly empty
     };
+    // Bounded waits for the loads that iteration it reads, d iterations
+    // from now: g row it+3 in ring position 3+d, f row it+1 in position
+    // F1+d (loaded once the segment needs it).  Every thread polls (letting
+    // one warp poll for all measured slower: at the kernel's register
+    // budget the branch spills).
+    auto wait_rows = [&](int it, int d) {
+        bool ok = mbar_wait(gbar(R.g[3 + d]), gpar(it));
+        if (it >= ys - 2) ok = mbar_wait(fbar(R.f[SM::F1 + d]), fpar(it)) && ok;
+        return ok;
+    };
 #pragma unroll
-    for (int d = 0; d < DEPTH; ++d) issue_for(yfirst + d, R.g[d + 3], R.f[d + SM::F1]);
+    for (int d = 0; d < DEPTH; ++d)
+        issue_for(yfirst + d, R.g[d + 3], R.f[d + SM::F1]);
 
     // Interior strips never wrap in x when pushing; interior rows never wrap
     // or bounce in y.
@@ -669,9 +790,22 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     T c_f[9] = {}, n_f[9] = {};  // own f values (FCARRY): row y, row y+1
 
     for (int y = yfirst; y < ye; ++y) {
-        cp_async_wait<DEPTH - 1>();   // g row y+3, f row y+1 have landed (own chunks)
-        __syncthreads();              // ... everyone's; rows y-1 are free
-        issue_for(y + DEPTH, R.g[SM::NBG - 1], R.f[SM::NBF - 1]);  // the slots of rows y-1
+        if (tma) {
+            // g row y+3 and (once the segment needs it) f row y+1 have landed
+            if (__syncthreads_or(!wait_rows(y, 0))) {  // rows y-1 are free; or a wait ran out
+                if (t == 0 && P.err) atomicOr(P.err, 1u);
+                // wait (bounded) for the loads still in flight into this
+                // CTA's shared memory, those of iterations y+1 .. y+DEPTH-1,
+                // so that none lands after the CTA has gone
+                for (int d = 1; d < DEPTH; ++d)
+                    if (y + d < ye) wait_rows(y + d, d);
+                return;
+            }
+        } else {
+            cp_async_wait<DEPTH - 1>();   // g row y+3, f row y+1 have landed (own chunks)
+            __syncthreads();              // ... everyone's; rows y-1 are free
+        }
+        issue_for(y + DEPTH, R.g[SM::NBG - 1], R.f[SM::NBF - 1]);
 
         // 1. phi at row y+3, columns -3 .. SW+2
         {
@@ -909,6 +1043,18 @@ k_strip(const char *__restrict__ src, char *__restrict__ dst, const __grid_const
     const int ys = P.ya + blockIdx.y * seg_h;
     strip_body<T, ST, SW, DEPTH, SLAB>(src, dst, P, blockIdx.x * SW, ys, min(ys + seg_h, P.yb),
                                        smem_raw);
+}
+
+// Single domain with tensor-tile staging of the population rows (FP32):
+// `map` describes the source level (x, row, slot).
+template <class T, class ST, int SW, int DEPTH>
+__global__ void __launch_bounds__(strip_threads(SW), (StripSmem<T, ST, SW, DEPTH>::MINB))
+k_strip_tma(const char *__restrict__ src, char *__restrict__ dst, const __grid_constant__ KP<T> P,
+            int seg_h, const __grid_constant__ CUtensorMap map) {
+    extern __shared__ __align__(128) char smem_raw[];
+    const int ys = P.ya + blockIdx.y * seg_h;
+    strip_body<T, ST, SW, DEPTH, false, true>(src, dst, P, blockIdx.x * SW, ys, min(ys + seg_h, P.yb),
+                                              smem_raw, &map);
 }
 
 // ---------------------------------------------------------------- batches

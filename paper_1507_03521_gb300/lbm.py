@@ -27,7 +27,8 @@ STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_NONFI
 EXPORTS = ["lbm_version", "lbm_buffer_sizes", "lbm_create", "lbm_bind_buffers", "lbm_init_phi",
            "lbm_step", "lbm_fields", "lbm_mass", "lbm_laplace", "lbm_state_bytes",
            "lbm_get_state", "lbm_set_state", "lbm_step_count", "lbm_last_error",
-           "lbm_create_error", "lbm_destroy", "lbm_mass_noalloc", "lbm_alu_peak",
+           "lbm_create_error", "lbm_destroy", "lbm_test_unfinished_tiles", "lbm_mass_noalloc",
+           "lbm_alu_peak",
            "lbm_batch_buffer_sizes", "lbm_batch_create", "lbm_batch_bind_buffers",
            "lbm_batch_init_phi", "lbm_batch_step", "lbm_batch_set_graph", "lbm_batch_set_segment",
            "lbm_batch_autotune", "lbm_batch_fields", "lbm_batch_mass", "lbm_batch_cells",
@@ -225,6 +226,8 @@ def _open(path: str):
     lib.lbm_adj_segment.argtypes = [_vp, ctypes.c_int64, _vp, ctypes.c_size_t, _vp, _vp, _vp]
     lib.lbm_adj_set_graph.restype = S
     lib.lbm_adj_set_graph.argtypes = [_vp, ctypes.c_int]
+    lib.lbm_test_unfinished_tiles.restype = S
+    lib.lbm_test_unfinished_tiles.argtypes = [_vp, ctypes.c_int]
     return lib
 
 
@@ -417,6 +420,11 @@ class Sim:
         lambda_{t0}."""
         self._check(self._lib.lbm_adj_segment(self._h, int(n), states.data_ptr(), int(level_stride),
                                               lam.data_ptr(), lam_tmp.data_ptr(), work.data_ptr()))
+
+    def test_unfinished_tiles(self, on: bool):
+        """Test hook: tile loads that never finish, so their bounded waits
+        run out (lbm_test_unfinished_tiles)."""
+        self._check(self._lib.lbm_test_unfinished_tiles(self._h, int(bool(on))))
 
     def adj_set_graph(self, on: bool):
         self._check(self._lib.lbm_adj_set_graph(self._h, int(bool(on))))

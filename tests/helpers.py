@@ -89,6 +89,23 @@ def check64_long(g, o, spread, tag, steps, keys=FIELDS):
     assert worst[0][0] <= 1.0, f"{tag}: {worst}"
 
 
+def same_result(a, b, dtype, tag=""):
+    """Two GPU runs of the same per-cell arithmetic in different kernels
+    (single domain, batch, slabs): bit for bit in FP64, built without
+    contracted multiply-adds, and in the 16-bit storage forms; within FP32
+    rounding in FP32 (the FP32 parity bar, 1e-5 of the field's scale),
+    where nvcc is free to contract a product and a sum into one FMA and
+    does not do it the same way in every kernel."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    if dtype == "f32":
+        scale = max(1.0, float(np.abs(a).max()))
+        err = float(np.abs(a.astype(np.float64) - b.astype(np.float64)).max())
+        assert err <= 1e-5 * scale, (tag, err, scale)
+    else:
+        assert np.array_equal(a, b), tag
+
+
 def fast_oracle(p):
     """The oracle, from its OpenMP build where the compiler has OpenMP (bit-
     identical to the serial build), else the serial build."""

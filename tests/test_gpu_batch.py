@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_1507_03521_gb300 import workloads as W
-from helpers import check64, oracle_spread
+from helpers import check64, oracle_spread, same_result
 
 pytestmark = pytest.mark.gpu
 
@@ -35,9 +35,11 @@ def _mixed():
 @pytest.mark.parametrize("dtype", ["f32", "f16s", "f64"])
 @pytest.mark.parametrize("graph", [False, True])
 def test_batch_equals_single_domain_runs(L, dtype, graph):
-    """Same kernel body per item: every domain of the batch is bit-identical
-    to stepping it alone, with or without CUDA-graph replay, for an odd
-    step count (so both parities and a plain launch occur)."""
+    """Same kernel body per item: every domain of the batch gives what
+    stepping it alone gives (bit for bit in FP64 and 16-bit storage, within
+    FP32 rounding in FP32, helpers.same_result), with or without CUDA-graph
+    replay, for an odd step count (so both parities and a plain launch
+    occur)."""
     doms = _mixed()
     b = L.Batch([p for p, _ in doms], dtype, graph=graph)
     b.init_phi([phi for _, phi in doms])
@@ -50,9 +52,12 @@ def test_batch_equals_single_domain_runs(L, dtype, graph):
         s.step(7)
         ref = s.fields(("phi", "ux", "uy", "p"))
         for k in ("phi", "ux", "uy", "p"):
-            assert np.array_equal(got[i][k].cpu().numpy(), ref[k].cpu().numpy()), (i, k)
+            same_result(got[i][k].cpu().numpy(), ref[k].cpu().numpy(), dtype, (i, k))
         sm, st = s.mass()
-        assert m[i] == sm and t[i] == st
+        if dtype == "f32":
+            assert abs(m[i] - sm) <= 1e-9 * abs(sm) and abs(t[i] - st) <= 1e-6 * max(1.0, abs(st))
+        else:
+            assert m[i] == sm and t[i] == st
     assert b.step_count == 7
     b.close()
 
@@ -82,8 +87,8 @@ def test_batch_item_split_between_strip_widths(L):
 
 @pytest.mark.parametrize("graph", [False, True])
 def test_batch_of_narrow_domains_only(L, graph):
-    """Every strip narrow (widths 8 .. 64): the 128-column launch is
-    skipped, and each domain is still bit-identical to stepping it alone."""
+    """Every strip narrow (widths 8 .. 64): the 64-column kernel runs, and
+    each domain still gives what stepping it alone gives."""
     doms = W.batch_domains(n=6, seed=91, sides=(64,))
     for nx, seed in ((8, 1), (40, 2), (56, 3)):
         p, phi, _, _ = W.small_case(nx, 30, seed=seed)
@@ -99,7 +104,7 @@ def test_batch_of_narrow_domains_only(L, graph):
         s.step(5)
         ref = s.fields(("phi", "ux", "uy", "p"))
         for k in ("phi", "ux", "uy", "p"):
-            assert np.array_equal(got[i][k].cpu().numpy(), ref[k].cpu().numpy()), (i, k)
+            same_result(got[i][k].cpu().numpy(), ref[k].cpu().numpy(), "f32", (i, k))
     b.close()
 
 

@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import check64, oracle_spread
+from helpers import check64, oracle_spread, same_result
 from paper_1507_03521_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -66,6 +66,10 @@ CASES = [
     ("strip_walls24x5", lambda: W.small_case(24, 5, seed=16, walls=True, gravity=1e-5, u_wall=0.02), 15),
     ("strip_walls200x45", lambda: W.small_case(200, 45, seed=17, walls=True, gravity=2e-5, u_wall=-0.01), 25),
     ("strip_walls8x70", lambda: W.small_case(8, 70, seed=18, walls=True, gravity=1e-5, u_wall=0.01), 20),
+    # 368 columns: strips 1 and 2 lie inside the level and take their rows
+    # by tensor tiles (FP32); strips 0 and 3 wrap and copy by chunks
+    ("tiles368x45", lambda: W.small_case(368, 45, seed=19), 20),
+    ("tiles_walls368x29", lambda: W.small_case(368, 29, seed=20, walls=True, gravity=1e-5, u_wall=0.01), 20),
 ]
 
 
@@ -283,3 +287,28 @@ def test_errors_surface_through_the_abi(lbm):
     with pytest.raises(lbm.LBMError) as e:
         s.mass()
     assert e.value.status == -3
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_tensor_tile_rows_equal_chunk_copies(lbm, walls):
+    """FP32 single domains stage the rows of strips that lie inside the
+    level by TMA tensor tiles; the batched form copies every row by 16-byte
+    chunks.  Same rows in shared memory and the same per-cell arithmetic,
+    so the two agree to FP32 rounding (different kernels may contract
+    multiply-adds differently; helpers.same_result)."""
+    p, phi, ux, uy = W.small_case(368, 61, seed=21, walls=walls, gravity=1e-5 if walls else 0.0,
+                                  u_wall=0.01 if walls else 0.0)
+    s = lbm.Sim(p, "f32")
+    s.init_phi(phi)
+    s.step(9)
+    a = {k: v.cpu().numpy() for k, v in s.fields(("phi", "ux", "uy", "p")).items()}
+    sm = s.mass()
+    s.close()
+    b = lbm.Batch([p], "f32")
+    b.init_phi([phi])
+    b.step(9)
+    g = b.fields()[0]
+    for k in a:
+        same_result(a[k], g[k].cpu().numpy(), "f32", k)
+    assert abs(b.mass()[0][0] - sm[0]) <= 1e-9 * abs(sm[0])
+    b.close()

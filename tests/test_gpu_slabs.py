@@ -1,8 +1,11 @@
 """The y-slab decomposition (lbm_slabs_*) against the whole-domain step.
 
 A domain split into slabs that step separately and exchange ghost rows on
-the device must reproduce the whole-domain state bit for bit: every cell
-runs the same kernel body, and the exchange only moves populations.  The
+the device must reproduce the whole-domain state: every cell runs the same
+kernel body, and the exchange only moves populations.  Bit for bit in FP64
+and the 16-bit forms; within FP32 rounding in FP32, where the slab kernel
+and the whole-domain kernel (which stages interior rows by tensor tiles)
+are compiled separately and nvcc may contract multiply-adds differently.  The
 cases cover periodic and wall-bounded domains (moving walls, gravity), even
 and uneven splits, the smallest slab (3 rows), one slab across the periodic
 wrap, interior strips (fast push path) and edge strips, and every storage
@@ -11,6 +14,7 @@ form.
 import numpy as np
 import pytest
 
+from helpers import same_result
 from paper_1507_03521_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -53,7 +57,10 @@ def _compare(L, p, phi, ux, uy, dtype, steps, **kw):
     assert step == steps and s.step_count == steps
     n = p["nx"] * p["ny"]
     for q, (x, y) in enumerate(zip(_slots(ref, dtype, n), _slots(got, dtype, n))):
-        assert np.array_equal(x, y), (dtype, q, kw)
+        if dtype == "f32":
+            same_result(x.view(np.float32), y.view(np.float32), dtype, (q, kw))
+        else:
+            assert np.array_equal(x, y), (dtype, q, kw)
     s.close()
     a.close()
 
