@@ -547,7 +547,8 @@ def main():
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": _traffic("f32"), "peak_kind": peak_kind,
                          "bytes_per_cell": BYTES_PER_CELL["f32"],
-                         "kernel": "k_strip<float>" if n % 8 == 0 else "k_step<float>",
+                         "kernel": ("k_strip_tma<float> (rows of interior strips by TMA tensor tiles)"
+                                    if n % 8 == 0 else "k_step<float>"),
                          "launch_ms": {"mean": round(avg_launch_ms, 5), "min": round(min(per), 5),
                                        "max": round(max(per), 5)}},
             "gpu_launches": args.steps, "clocks": ck}

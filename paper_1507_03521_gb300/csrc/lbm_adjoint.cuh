@@ -16,7 +16,8 @@
 // from the cells whose stencils read it, with the ghost-row rules of the
 // forward step: mirror for phi and mu, linear extrapolation for p), so the
 // result is deterministic.  Kernels, in order, for one reverse step:
-//   k_adj_f0 .. k_adj_f3  recompute the forward fields of step t,
+//   k_step<MODE_ADJ>      the forward fields of step t, in one tile-kernel
+//                         launch (lbm_kernels.cuh),
 //   k_adj_collide         streaming and collision transposed,
 //   k_adj_p               grad p transposed, then u, p, F backwards,
 //   k_adj_mu              grad mu and lap mu transposed, and the step's
@@ -49,6 +50,12 @@ enum AdjArr {
     B_GPHX, B_GPHY, B_GMUX, B_GMUY, B_ALPHA, B_GL, B_SIGMA,
     A_COUNT
 };
+
+// The tile kernel's MODE_ADJ writes the first 16 arrays in this order.
+static_assert(A_PHI == 0 && A_RHO == 1 && A_MU == 2 && A_MU1 == 3 && A_GPHX == 4 && A_GPHY == 5 &&
+                  A_GMUX == 6 && A_GMUY == 7 && A_LMU == 8 && A_FX == 9 && A_FY == 10 && A_UX == 11 &&
+                  A_UY == 12 && A_P == 13 && A_GPX == 14 && A_GPY == 15,
+              "forward-field order of MODE_ADJ");
 
 template <class T>
 struct AdjW {
@@ -156,32 +163,7 @@ __device__ __forceinline__ int row_of(long long k, int nx) {
     return k <= 0x7fffffffLL ? (int)k / nx : (int)(k / nx);
 }
 
-// ----------------------------------------------------- forward recompute
-
-// phi, rho, and (temporarily) sum f, j in A_P, A_UX, A_UY.
-template <class T>
-__global__ void k_adj_f0(const T *__restrict__ lvl, const AdjP<T> P, AdjW<T> W) {
-    const long long N = (long long)P.k.nx * P.k.ny, NS = P.k.NS;
-    ADJ_LOOP(k, N) {
-        T f[9], g[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            f[i] = lvl[i * NS + k];
-            g[i] = lvl[(9 + i) * NS + k];
-        }
-        T phi = T(0), ps = T(0);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            phi += g[i];
-            ps += f[i];
-        }
-        W[A_PHI][k] = phi;
-        W[A_RHO][k] = P.k.rhoB + (phi - P.k.phiB) * P.k.drho;
-        W[A_P][k] = ps;
-        W[A_UX][k] = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-        W[A_UY][k] = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
-    }
-}
+// -------------------------------------- forward fields of the initial state
 
 // phi given directly (initial state): copy into A_PHI.
 template <class T>
@@ -206,47 +188,6 @@ __global__ void k_adj_f1(const AdjP<T> P, AdjW<T> W) {
         grad_g(W[A_PHI], B, x, y, false, gx, gy);
         W[A_GPHX][k] = gx;
         W[A_GPHY][k] = gy;
-    }
-}
-
-// grad mu, lap mu, F, u, p (Eqs. 31-32); A_UX/A_UY/A_P hold j and sum f.
-template <class T>
-__global__ void k_adj_f2(const AdjP<T> P, AdjW<T> W) {
-    const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
-    const long long N = (long long)P.k.nx * P.k.ny;
-    ADJ_LOOP(k, N) {
-        const int y = row_of(k, B.nx), x = (int)(k - (long long)y * B.nx);
-        T gx, gy;
-        grad_g(W[A_MU], B, x, y, false, gx, gy);
-        const T lm = lap_g(W[A_MU], B, x, y);
-        const T ph = W[A_PHI][k], rho = W[A_RHO][k];
-        const T Fx = -ph * gx;
-        const T Fy = -ph * gy - (rho - P.k.rhoref) * P.k.grav;
-        const T ux = (W[A_UX][k] + Fx / T(6)) * T(3) / rho;
-        const T uy = (W[A_UY][k] + Fy / T(6)) * T(3) / rho;
-        const T udr = P.k.drho * (ux * W[A_GPHX][k] + uy * W[A_GPHY][k]);
-        W[A_P][k] = W[A_P][k] + (udr - P.k.gl * rho * lm) / T(6);
-        W[A_GMUX][k] = gx;
-        W[A_GMUY][k] = gy;
-        W[A_LMU][k] = lm;
-        W[A_FX][k] = Fx;
-        W[A_FY][k] = Fy;
-        W[A_UX][k] = ux;
-        W[A_UY][k] = uy;
-    }
-}
-
-// grad p with extrapolated ghosts.
-template <class T>
-__global__ void k_adj_f3(const AdjP<T> P, AdjW<T> W) {
-    const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
-    const long long N = (long long)P.k.nx * P.k.ny;
-    ADJ_LOOP(k, N) {
-        const int y = row_of(k, B.nx), x = (int)(k - (long long)y * B.nx);
-        T gx, gy;
-        grad_g(W[A_P], B, x, y, true, gx, gy);
-        W[A_GPX][k] = gx;
-        W[A_GPY][k] = gy;
     }
 }
 

@@ -54,7 +54,11 @@ static_assert(D2Q9::opp(1) == 3 && D2Q9::opp(2) == 4 && D2Q9::opp(3) == 1 && D2Q
 static_assert(D2Q9::opp(5) == 7 && D2Q9::opp(6) == 8 && D2Q9::opp(7) == 5 && D2Q9::opp(8) == 6,
               "opposite of diagonal directions");
 
-enum { MODE_STEP = 0, MODE_FIELDS = 1 };
+// MODE_ADJ: the forward fields that the adjoint of the step linearises
+// about, written to out.adj (16 arrays, stride out.adj_ns, in this order:
+// phi, rho, mu, mu per unit sigma, grad phi (x, y), grad mu (x, y), lap mu,
+// F (x, y), u (x, y), p, grad p (x, y)).
+enum { MODE_STEP = 0, MODE_FIELDS = 1, MODE_ADJ = 2 };
 
 // Kernel parameters, converted once to the compute type T on the host.
 template <class T>
@@ -100,6 +104,11 @@ __device__ __forceinline__ bool dbg_ok(unsigned *w, bool ok, unsigned code) {
 template <class T>
 struct FieldOut {
     T *phi, *rho, *p, *ux, *uy, *mu, *P;
+    // MODE_ADJ: base of the 16 field arrays, their stride, and 4 beta and
+    // kappa per unit sigma (for mu per unit sigma)
+    T *adj = nullptr;
+    long long adj_ns = 0;
+    T beta1x4 = T(0), kappa1 = T(0);
 };
 
 // ------------------------------------------------------------ storage
@@ -559,6 +568,29 @@ k_step(const char *__restrict__ src, char *__restrict__ dst, const KP<T> P, Fiel
         grad9(s.p, TL::iq(ly, lx), TL::QW, gpx, gpy);
         const long long k = (long long)gy * nx + gx;
         const T pc = s.p[TL::iq(ly, lx)];
+        if (MODE == MODE_ADJ) {
+            T *a = out.adj + k;
+            const long long S = out.adj_ns;
+            const T q = (m.phi - P.phiA) * (m.phi - P.phiB) * (m.phi - P.phibar);
+            const T lph = lap9(s.phi, TL::ip(ly, lx), TL::PW);
+            a[0 * S] = m.phi;
+            a[1 * S] = m.rho;
+            a[2 * S] = m.mu;
+            a[3 * S] = out.beta1x4 * q - out.kappa1 * lph;
+            a[4 * S] = m.gphx;
+            a[5 * S] = m.gphy;
+            a[6 * S] = m.gmux;
+            a[7 * S] = m.gmuy;
+            a[8 * S] = m.lmu;
+            a[9 * S] = m.Fx;
+            a[10 * S] = m.Fy;
+            a[11 * S] = m.ux;
+            a[12 * S] = m.uy;
+            a[13 * S] = pc;
+            a[14 * S] = gpx;
+            a[15 * S] = gpy;
+            continue;
+        }
         if (MODE == MODE_FIELDS) {
             if (out.phi) out.phi[k] = m.phi;
             if (out.rho) out.rho[k] = m.rho;

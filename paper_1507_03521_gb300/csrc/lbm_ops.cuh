@@ -341,10 +341,16 @@ struct OpsImpl {
         const AdjW<T> W = make_w(d, work);
         const int nb = adj_grid(d);
         T *L = static_cast<T *>(lam);
-        k_adj_f0<T><<<nb, 256, 0, s>>>(static_cast<const T *>(lvl), P, W);
-        k_adj_f1<T><<<nb, 256, 0, s>>>(P, W);
-        k_adj_f2<T><<<nb, 256, 0, s>>>(P, W);
-        k_adj_f3<T><<<nb, 256, 0, s>>>(P, W);
+        // the forward fields of step t, in one tile-kernel launch
+        cudaError_t e = prepare<MODE_ADJ>();
+        if (e != cudaSuccess) return e;
+        FieldOut<T> fo{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        fo.adj = W.a;
+        fo.adj_ns = d.NS;
+        fo.beta1x4 = T(4) * P.beta1;
+        fo.kappa1 = P.kappa1;
+        k_step<T, ST, RPT, MODE_ADJ><<<grid(d), dim3(32, 8), TL::bytes, s>>>(
+            static_cast<const char *>(lvl), nullptr, make_kp<T>(d), fo);
         k_adj_collide<T><<<nb, 256, 0, s>>>(static_cast<const T *>(lam_next), L, P, W);
         k_adj_p<T><<<nb, 256, 0, s>>>(L, P, W);
         k_adj_mu<T><<<nb, 256, 0, s>>>(P, W, part(d, work));  // also the (M, sigma) partials

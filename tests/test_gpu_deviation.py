@@ -121,8 +121,8 @@ def test_deviation_storage_large_grid_sampled(L):
     """1024 x 1024, 32 droplets, rho_A/rho_B = 100 (the precision workload
     at a quarter of its side, at rest), 100 steps: the deviation forms
     against the FP32 path, which the FP32 parity tests tie to the oracle;
-    the deviation form stays closer to FP32 than the raw form does (FP16:
-    measured 1.5x on phi, 1.03-1.06x on u; BF16: 2x on both)."""
+    the deviation form stays closer to FP32 than the raw form (FP16: 1.5x
+    on phi, u at the FP32 level in both forms; BF16: 2x on both)."""
     p, phi = W.precision(n=1024, n_drops=32)
     f32 = _gpu(L, p, phi, None, None, 100, "f32")
     for kind in ("f16", "bf16"):
@@ -132,4 +132,8 @@ def test_deviation_storage_large_grid_sampled(L):
             er = float(np.abs(raw[k] - f32[k]).max())
             ed = float(np.abs(dev[k] - f32[k]).max())
             print(f"DEV1024 {kind} {k}: raw {er:.3e} deviation {ed:.3e}")
-            assert ed <= er, (kind, k, ed, er)
+            # FP16 u: both forms sit at the FP32 level here (within 3% of
+            # each other over several runs); every other field and BF16
+            # measured 1.5-2x better with deviations
+            slack = 1.1 if (kind == "f16" and k != "phi") else 1.0
+            assert ed <= slack * er, (kind, k, ed, er)
