@@ -477,11 +477,13 @@ struct StripSmem {
     // compiler is held to, so that registers do not become the tighter
     // limit; otherwise (0) the compiler's own choice stands.
     static constexpr int MINB = FCARRY ? int(233472 / (bytes + 1024)) : 0;
-    // tensor-tile staging: one mbarrier per ring slot (g slots, then f
-    // slots) after the rings; the row buffers of a TMA load must start on
-    // 128-byte boundaries, and so must the rows
+    // tensor-tile staging: the rows issued in one iteration (a g row and an
+    // f row) complete on one mbarrier; DEPTH + 1 barriers after the rings
+    // are reused in turn.  The row buffers of a TMA load must start on
+    // 128-byte boundaries.
+    static constexpr int NBAR = DEPTH + 1;
     static constexpr size_t bar_off = (bytes + 7) / 8 * 8;
-    static constexpr size_t bytes_tma = bar_off + 8 * (size_t)(NBG + NBF);
+    static constexpr size_t bytes_tma = bar_off + 8 * (size_t)NBAR;
     static constexpr bool TMA_ROWS = gb % 128 == 0 && fb % 128 == 0;
 };
 
@@ -710,7 +712,7 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
         static_assert(SM::TMA_ROWS, "TMA rows need 128-byte aligned row buffers");
         bars = smem_u32(smem_raw + SM::bar_off);
         if (tma && t == 0) {
-            for (int k = 0; k < SM::NBG + SM::NBF; ++k) mbar_init(bars + 8 * k, 1);
+            for (int k = 0; k < SM::NBAR; ++k) mbar_init(bars + 8 * k, 1);
             mbar_init_fence();
         }
     }
@@ -719,18 +721,11 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     RingSlots<SM> R;
     auto at = [&](int off) { return smem_raw + off; };
     auto atT = [&](int off) { return reinterpret_cast<T *>(smem_raw + off); };
-    // barrier of the g slot at byte offset o, of the f slot at o
-    auto gbar = [&](int o) { return bars + 8u * (unsigned)(o / (int)SM::gb); };
-    auto fbar = [&](int o) {
-        return bars + 8u * (unsigned)(SM::NBG + (o - (int)(SM::gb * SM::NBG)) / (int)SM::fb);
-    };
-    // Phase parities follow from the iteration: a g slot is filled and
-    // consumed once every NBG iterations from yfirst on, an f slot once
-    // every NBF iterations from ys - 2 on (the first f row a segment loads
-    // is read at iteration ys - 2).
-    auto gpar = [&](int it) { return (unsigned)((it - yfirst) / SM::NBG) & 1u; };
-    auto fpar = [&](int it) { return (unsigned)((it - (ys - 2)) / SM::NBF) & 1u; };
-
+    // Barrier and phase parity of the rows issued for iteration it: the
+    // NBAR barriers are used in turn from yfirst on, each once every NBAR
+    // iterations.
+    auto ibar = [&](int it) { return bars + 8u * (unsigned)((it - yfirst) % SM::NBAR); };
+    auto ipar = [&](int it) { return (unsigned)((it - yfirst) / SM::NBAR) & 1u; };
     // Iteration y reads g row y+3 and f row y+1 first; both are issued
     // DEPTH iterations earlier, as one commit group.  The collisions of the
     // segment need p from row ys-1 on, so the f rows of the first warm-up
@@ -739,19 +734,17 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     auto issue_for = [&](int it, int gslot, int fslot) {
         const int gr = it + 3, fr = it + 1;
         if (tma) {
-            if (gr <= ye + 2) {
-                const int b = buf_row<SLAB>(P, gr);
-                if (t == 0 && LBM_IDX_OK(P, b >= 0 && b < lvl_rows, 1)) {
-                    mbar_expect_tx(gbar(gslot), (unsigned)(9 * SR::LW * sizeof(T)) + P.tx_extra);
-                    tma_load_3d(smem_u32(at(gslot)), map, gbar(gslot), x0 - HP, b, 9);
-                }
-            }
-            if (fr >= ys - 1 && fr <= ye) {
-                const int b = buf_row<SLAB>(P, fr);
-                if (t == 0 && LBM_IDX_OK(P, b >= 0 && b < lvl_rows, 1)) {
-                    mbar_expect_tx(fbar(fslot), (unsigned)(9 * SR::LW * sizeof(T)) + P.tx_extra);
-                    tma_load_3d(smem_u32(at(fslot)), map, fbar(fslot), x0 - HP, b, 0);
-                }
+            // one arrival announcing both rows' bytes, then the two loads
+            const bool g_in = gr <= ye + 2, f_in = fr >= ys - 1 && fr <= ye;
+            if (t == 0 && (g_in || f_in)) {
+                const int bg = buf_row<SLAB>(P, gr), bf = buf_row<SLAB>(P, fr);
+                const bool gok = g_in && LBM_IDX_OK(P, bg >= 0 && bg < lvl_rows, 1);
+                const bool fok = f_in && LBM_IDX_OK(P, bf >= 0 && bf < lvl_rows, 1);
+                constexpr unsigned row_bytes = (unsigned)(9 * SR::LW * sizeof(T));
+                const unsigned bar = ibar(it);
+                mbar_expect_tx(bar, (gok ? row_bytes : 0u) + (fok ? row_bytes : 0u) + P.tx_extra);
+                if (gok) tma_load_3d(smem_u32(at(gslot)), map, bar, x0 - HP, bg, 9);
+                if (fok) tma_load_3d(smem_u32(at(fslot)), map, bar, x0 - HP, bf, 0);
             }
             return;
         }
@@ -765,16 +758,11 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
         }
         cp_async_commit();  // one group per iteration, possibly empty
     };
-    // Bounded waits for the loads that iteration it reads, d iterations
-    // from now: g row it+3 in ring position 3+d, f row it+1 in position
-    // F1+d (loaded once the segment needs it).  Every thread polls (letting
-    // one warp poll for all measured slower: at the kernel's register
-    // budget the branch spills).
-    auto wait_rows = [&](int it, int d) {
-        bool ok = mbar_wait(gbar(R.g[3 + d]), gpar(it));
-        if (it >= ys - 2) ok = mbar_wait(fbar(R.f[SM::F1 + d]), fpar(it)) && ok;
-        return ok;
-    };
+    // Bounded wait for the rows that iteration it reads (g row it+3, and
+    // f row it+1 once the segment needs it), issued for it together.
+    // Every thread polls (letting one warp poll for all measured slower:
+    // at the kernel's register budget the branch spills).
+    auto wait_rows = [&](int it) { return mbar_wait(ibar(it), ipar(it)); };
 #pragma unroll
     for (int d = 0; d < DEPTH; ++d)
         issue_for(yfirst + d, R.g[d + 3], R.f[d + SM::F1]);
@@ -792,13 +780,13 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     for (int y = yfirst; y < ye; ++y) {
         if (tma) {
             // g row y+3 and (once the segment needs it) f row y+1 have landed
-            if (__syncthreads_or(!wait_rows(y, 0))) {  // rows y-1 are free; or a wait ran out
+            if (__syncthreads_or(!wait_rows(y))) {  // rows y-1 are free; or a wait ran out
                 if (t == 0 && P.err) atomicOr(P.err, 1u);
                 // wait (bounded) for the loads still in flight into this
                 // CTA's shared memory, those of iterations y+1 .. y+DEPTH-1,
                 // so that none lands after the CTA has gone
                 for (int d = 1; d < DEPTH; ++d)
-                    if (y + d < ye) wait_rows(y + d, d);
+                    if (y + d < ye) wait_rows(y + d);
                 return;
             }
         } else {
