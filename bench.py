@@ -53,9 +53,11 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-# Sources that define the step kernels (k_strip, k_step) and their launch.
+# Sources that define the step kernels (k_strip, k_step, k_strip_batch) and
+# their launch, with the batch work list and the slab launches.
 STEP_SOURCES = ("lbm_internal.h", "lbm_kernels.cuh", "lbm_strip.cuh", "lbm_strip_lag.cuh",
-                "lbm_ops.cuh", "lbm_f64.cu", "lbm_f32.cu", "lbm_f16.cu", "lbm_f16d.cu")
+                "lbm_ops.cuh", "lbm_f64.cu", "lbm_f32.cu", "lbm_f16.cu", "lbm_f16d.cu",
+                "lbm_batch.cu", "lbm_slabs.cu")
 
 
 # Sources of the D3Q19 step kernels and their launch.

@@ -196,8 +196,10 @@ __global__ void k_adj_f1(const AdjP<T> P, AdjW<T> W) {
 // Streaming and collision transposed.  lam_next: lambda_{t+1}; lam: output
 // lambda_t (partial: the direct (1 - 1/tau) terms; k_adj_p and k_adj_phi
 // add the terms through p, j and phi).
+// FP32: 3 CTAs per SM (80 registers) instead of 2 at the compiler's 128
+// registers measured 7% faster over the whole backward pass at 512^2.
 template <class T>
-__global__ void k_adj_collide(const T *__restrict__ lam_next, T *__restrict__ lam, const AdjP<T> P,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_collide(const T *__restrict__ lam_next, T *__restrict__ lam, const AdjP<T> P,
                               AdjW<T> W) {
     const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
     const long long N = (long long)P.k.nx * P.k.ny, NS = P.k.NS;
@@ -312,8 +314,10 @@ __global__ void k_adj_collide(const T *__restrict__ lam_next, T *__restrict__ la
 
 // grad p transposed (extrapolated ghosts) gives the full adjoint of p; then
 // p, u, F backwards (Eqs. 31-32) and the f terms through sum f and j.
+// FP32: 4 CTAs per SM (64 registers) instead of 3 at 80 registers measured
+// 7% faster over the whole backward pass at 512^2.
 template <class T>
-__global__ void k_adj_p(T *__restrict__ lam, const AdjP<T> P, AdjW<T> W) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_adj_p(T *__restrict__ lam, const AdjP<T> P, AdjW<T> W) {
     const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
     const long long N = (long long)P.k.nx * P.k.ny, NS = P.k.NS;
     const KP<T> &K = P.k;

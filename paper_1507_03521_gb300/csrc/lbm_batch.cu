@@ -1,11 +1,11 @@
 // lbm_batch.cu — the batched form of the C ABI (include/lbm.h, lbm_batch_*).
 //
 // Many independent domains (each with its own size and parameters, one
-// storage type for the whole batch) advance together: per time step a
+// storage type for the whole batch) advance together: per time step one
 // persistent launch of the batched strip kernel works through a list of
-// (domain, strip, segment) items, and a second one, of the narrow-strip
-// kernel, through the strips of at most 64 active columns.  Optionally the
-// launches are replayed from a CUDA graph.  Host-side bookkeeping only; every step of
+// (domain, strip, segment) items (the narrow-strip kernel when every strip
+// has at most 64 active columns).  Optionally the launches are replayed
+// from a CUDA graph.  Host-side bookkeeping only; every step of
 // the method runs in the kernels of lbm_strip.cuh / lbm_kernels.cuh.
 #include <cuda_runtime.h>
 
@@ -109,8 +109,8 @@ struct lbm_batch {
     int64_t steps = 0;
     bool initialized = false;
     int seg_h = 64;
-    int nitems = 0;    // items of the strip_width kernel, first in the item array
-    int nitems_n = 0;  // items of the narrow kernel, after them
+    int nitems = 0;    // items of more than narrow_width active columns
+    int nitems_n = 0;  // items of at most narrow_width active columns
     bool items_ready = false;
     bool use_graph = false;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // two steps starting at parity 0 / 1
@@ -146,45 +146,53 @@ struct lbm_batch {
 
 namespace {
 
-// Work lists for segment height seg_h, each sorted by decreasing cost so
-// that the persistent grid's CTAs, claiming items in order, take the
-// longest first.  A strip of at most narrow_width active columns goes to
-// the narrow kernel's list when the form has one.
+// The work list for segment height seg_h.  A strip of at most narrow_width
+// active columns counts as narrow when the form has a narrow kernel (used
+// only when every strip is narrow).  The persistent grid's CTAs claim items
+// in list order.  Each domain's items stay together, domains in order of
+// decreasing longest item, so that the strips and segments of one domain
+// run at the same time and share in L2 the halo columns and warm-up rows
+// they both read, and the sectors both write at a strip edge: at segment
+// height 96 the 1024-domain workload moved 1.13x its algorithmic DRAM bytes
+// per step, against 1.21x with all items sorted longest first (wide, then
+// narrow).
 lbm_status build_items(lbm_batch *b) {
     const int SW = b->ops->strip_width;
     const int NW = b->ops->batch_step_narrow ? b->ops->narrow_width : 0;
-    std::vector<BatchItem> it[2];
-    std::vector<long long> cost[2];
-    for (size_t i = 0; i < b->P.d.size(); ++i) {
+    const size_t nd = b->P.d.size();
+    std::vector<std::vector<BatchItem>> per(nd);
+    std::vector<long long> dcost(nd, 0);
+    int nwide = 0, nnarrow = 0;
+    for (size_t i = 0; i < nd; ++i) {
         const Derived &d = b->P.d[i];
         const int nseg = (d.ny + b->seg_h - 1) / b->seg_h;
         const int h = (d.ny + nseg - 1) / nseg;  // balanced segment height
         for (int x0 = 0; x0 < d.nx; x0 += SW) {
             const int w = std::min(SW, d.nx - x0);
-            const int k = w <= NW ? 1 : 0;
             for (int ys = 0; ys < d.ny; ys += h) {
                 const int ye = std::min(ys + h, d.ny);
-                it[k].push_back(BatchItem{(int)i, x0, ys, ye});
-                cost[k].push_back((long long)w * (ye - ys + 6));
+                const long long c = (long long)w * (ye - ys + 6);
+                per[i].push_back(BatchItem{(int)i, x0, ys, ye});
+                dcost[i] = std::max(dcost[i], c);
+                ++(w <= NW ? nnarrow : nwide);
             }
         }
     }
-    if ((int)(it[0].size() + it[1].size()) > b->P.max_items)
+    if (nwide + nnarrow > b->P.max_items)
         return b->fail(LBM_ERR_ARG, "segment height too small");
     std::vector<BatchItem> sorted;
-    for (int k = 0; k < 2; ++k) {
-        std::vector<int> order(it[k].size());
-        for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-        std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[k][a] > cost[k][c]; });
-        for (int o : order) sorted.push_back(it[k][o]);
-    }
+    sorted.reserve((size_t)(nwide + nnarrow));
+    std::vector<int> order(nd);
+    for (size_t i = 0; i < nd; ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return dcost[a] > dcost[c]; });
+    for (int o : order) sorted.insert(sorted.end(), per[o].begin(), per[o].end());
     LBMB_CK(b, cudaMemcpyAsync(b->items(), sorted.data(), sorted.size() * sizeof(BatchItem),
                                cudaMemcpyHostToDevice, b->stream));
     // new item counts change the tickets per step: restart both counters
     LBMB_CK(b, cudaMemsetAsync(b->tickets(), 0, 2 * sizeof(unsigned long long), b->stream));
     LBMB_CK(b, cudaStreamSynchronize(b->stream));
-    b->nitems = (int)it[0].size();
-    b->nitems_n = (int)it[1].size();
+    b->nitems = nwide;
+    b->nitems_n = nnarrow;
     b->items_ready = true;
     b->drop_graphs();
     return LBM_OK;

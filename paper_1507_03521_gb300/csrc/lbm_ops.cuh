@@ -10,6 +10,14 @@
 #include "lbm_strip.cuh"
 #include "lbm_strip_lag.cuh"
 
+// Shortest segment a strip CTA marches (rows) when the one-wave grid would
+// cut the strips finer.  Each segment re-reads 6 warm-up rows, but the grids
+// that need segments this short are small enough to sit in L2, where the
+// wider grid wins: FP32 at 512^2 ran 12.8k MLUPS with 4-row segments, 11.1k
+// with 8 and 8.0k with 16 (256^2: 4.2k, 3.6k, 2.1k); from 1024^2 up the
+// one-wave segments are longer than 16 rows anyway.
+constexpr int kSegMinRows = 4;
+
 namespace lbm {
 
 template <class T>
@@ -80,7 +88,7 @@ struct OpsImpl {
     }
 
     // Opt in to the strip kernel's shared memory and size the grid to
-    // one wave: strips x segments ~= resident CTAs, segments >= 16 rows.
+    // one wave: strips x segments ~= resident CTAs, segments >= kSegMinRows rows.
     template <bool SLAB>
     static cudaError_t strip_grid(const Derived &d, dim3 &grid, int &seg_h) {
         static PerDevice<StripCfg> cfg;
@@ -92,14 +100,14 @@ struct OpsImpl {
         one_wave(d, c, grid, seg_h);
         return cudaSuccess;
     }
-    // strips x segments ~= the resident CTAs c allows, segments >= 16 rows
+    // strips x segments ~= the resident CTAs c allows, segments >= kSegMinRows rows
     static void one_wave(const Derived &d, const StripCfg &c, dim3 &grid, int &seg_h) {
         const int strips = (d.nx + SW - 1) / SW;
         const int rows = d.yb - d.ya;  // rows stepped
         long long slots = (long long)c.per_sm * c.sms / (d.share > 1 ? d.share : 1);
         long long nseg = slots / strips;
         if (nseg < 1) nseg = 1;
-        const long long max_seg = (rows + 15) / 16;
+        const long long max_seg = (rows + kSegMinRows - 1) / kSegMinRows;
         if (nseg > max_seg) nseg = max_seg;
         seg_h = (int)((rows + nseg - 1) / nseg);
         nseg = (rows + seg_h - 1) / seg_h;

@@ -472,11 +472,14 @@ struct StripSmem {
     static constexpr size_t bytes = pop_bytes + fld_elems * sizeof(T);
     // Order in shared memory: NBG g rows, NBF f rows, then the phi, mu and
     // p rings (RingSlots holds the offsets).
-    // With the f carry, the CTAs per SM that the shared memory allows (228
-    // KB per SM, 1 KB per CTA reserved) become the register budget the
-    // compiler is held to, so that registers do not become the tighter
-    // limit; otherwise (0) the compiler's own choice stands.
-    static constexpr int MINB = FCARRY ? int(233472 / (bytes + 1024)) : 0;
+    // With the f carry, and for the deviation storage, the CTAs per SM that
+    // the shared memory allows (228 KB per SM, 1 KB per CTA reserved) become
+    // the register budget the compiler is held to, so that registers do not
+    // become the tighter limit; otherwise (0) the compiler's own choice
+    // stands.  (The deviation kernels would take 96 registers, 5 CTAs per
+    // SM; at 80 they spill 16-20 bytes and measured 1% (FP16) and 3% (BF16)
+    // faster with 6.)
+    static constexpr int MINB = (FCARRY || DEV) ? int(233472 / (bytes + 1024)) : 0;
     // tensor-tile staging: the rows issued in one iteration (a g row and an
     // f row) complete on one mbarrier; DEPTH + 1 barriers after the rings
     // are reused in turn.  The row buffers of a TMA load must start on
