@@ -212,8 +212,9 @@ LBM_API lbm_status lbm_test_unfinished_tiles(lbm_sim *sim, int on);
  * surface tension (kappa and beta proportional to it).  All pointers are
  * device pointers; state and lambda buffers are lbm_state_bytes() each and
  * lam_next must differ from lam_t.  `work` is a caller-owned device buffer
- * of lbm_adj_work_bytes() bytes, 256-byte aligned, holding scratch fields
- * and the running totals (lbm_adj_reset zeroes them).  Asynchronous on the
+ * of lbm_adj_work_bytes() bytes, 256-byte aligned, holding scratch fields,
+ * the running totals and a counter of the reverse-step kernels; call
+ * lbm_adj_reset (which zeroes both) before a buffer's first use.  Asynchronous on the
  * handle's stream except lbm_adj_grads and a seed that returns the loss.
  * The step being differentiated is the synchronous step of Eqs. 22-32
  * (Sec. 3) with its moment, stencil and wall rules; the paper itself has

@@ -20,11 +20,11 @@
 //                         launch (lbm_kernels.cuh),
 //   k_adj_collide         streaming and collision transposed,
 //   k_adj_p               grad p transposed, then u, p, F backwards,
-//   k_adj_mu              grad mu and lap mu transposed, and the step's
-//                         per-block (M, sigma) partial sums,
-//   k_adj_phi             grad phi and lap phi transposed, phi = sum g,
+//   k_adj_muphi           grad mu and lap mu transposed, then grad phi and
+//                         lap phi transposed and phi = sum g, per tile; the
+//                         step's (M, sigma) sums, folded by its last CTA,
 //   k_adj_theta           per-cell (M, sigma) terms reduced in FP64 (the
-//                         initial state's; a step's come from k_adj_mu).
+//                         initial state's; a step's come from k_adj_muphi).
 // M enters through alpha = M / (cs2 (tau_g - 1/2)) and gamma lambda with
 // lambda = M (Eq. 33); sigma through kappa and beta, both proportional to
 // sigma (Eqs. 3-4 solved), so mu = sigma mu1.
@@ -151,6 +151,12 @@ __device__ __forceinline__ T tgather(const Nb<T> &B, int x, int y, bool extrap, 
         }
     }
     return acc;
+}
+
+// x mod n in [0, n), for any x
+__device__ __forceinline__ int adj_wrap(int x, int n) {
+    x %= n;
+    return x < 0 ? x + n : x;
 }
 
 #define ADJ_LOOP(k, N)                                                            \
@@ -386,55 +392,103 @@ __device__ __forceinline__ void adj_theta_partials(double dM, double dS, double 
     }
 }
 
-// grad mu and lap mu transposed (mirror ghosts): full adjoint of mu; the
-// sigma term mu1 * mu_bar.  The step's (M, sigma) terms of a cell are final
-// here (alpha_bar and (gamma lambda)_bar come from the collision and p
-// passes), so this pass also writes their per-block partial sums (the
-// reduction k_adj_theta does for the initial state).
+// The mu and phi adjoints of a reverse step, and the fold of its (M, sigma)
+// partial sums, in one launch.  A CTA of 256 threads takes
+// 32 x 8 tiles in turn: it computes mu_bar on the tile and a ring of one
+// cell into shared memory (the ring cells are recomputed by each
+// neighbouring tile and only read here), then the phi adjoint of the tile
+// from it.  Its inputs are final before the launch; its global writes are
+// the tile cells' lambda_t g slots and the CTA's (M, sigma) partial sums.
+// The last CTA to finish (a ticket counter; the counter is left at zero)
+// folds the partial sums into the running totals, in the same fixed order
+// as k_adj_accumulate.
+constexpr int kMpTX = 32, kMpTY = 8;
+
 template <class T>
-__global__ void __launch_bounds__(256) k_adj_mu(const AdjP<T> P, AdjW<T> W, double *__restrict__ part) {
+__global__ void __launch_bounds__(256) k_adj_muphi(T *__restrict__ lam, const AdjP<T> P, AdjW<T> W,
+                                                   double *__restrict__ part, double *__restrict__ acc,
+                                                   unsigned *__restrict__ ticket) {
+    constexpr int HX = kMpTX + 2, HY = kMpTY + 2;
+    __shared__ T smu[HY][HX];
+    __shared__ bool last;
     const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
-    const long long N = (long long)P.k.nx * P.k.ny;
-    const T *gx = W[B_GMUX], *gy = W[B_GMUY], *bl = W[B_LMU];
-    double dM = 0.0, dS = 0.0;
+    const KP<T> &K = P.k;
+    const long long NS = K.NS;
+    const int nx = B.nx, ny = B.ny;
+    const int tid = threadIdx.x, lx = tid % kMpTX, ly = tid / kMpTX;  // 1-D block of 256
+    const int tilesx = (nx + kMpTX - 1) / kMpTX, tilesy = (ny + kMpTY - 1) / kMpTY;
+    const long long ntiles = (long long)tilesx * tilesy;
+    const T *gmx = W[B_GMUX], *gmy = W[B_GMUY], *bl = W[B_LMU];
+    const T *gpx = W[B_GPHX], *gpy = W[B_GPHY];
     const double a1 = (double)P.alpha1, gm = (double)P.gamma;
-    ADJ_LOOP(k, N) {
-        const int y = row_of(k, B.nx), x = (int)(k - (long long)y * B.nx);
-        const T t = tgather(B, x, y, false, [&](long long c, int i, T coef) {
-            return coef * (T(3.0 * D2Q9::w(i)) * (T(D2Q9::cx(i)) * gx[c] + T(D2Q9::cy(i)) * gy[c]) +
-                           T(6.0 * D2Q9::w(i)) * bl[c]);
-        });
-        const T bmu = W[B_MU][k] + t - T(10.0 / 3.0) * bl[k];
-        const T bsig = bmu * W[A_MU1][k];
-        W[B_MU][k] = bmu;
-        W[B_SIGMA][k] = bsig;
-        dM += a1 * (double)W[B_ALPHA][k] + gm * (double)W[B_GL][k];
-        dS += (double)bsig;
+    double dM = 0.0, dS = 0.0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int tx0 = (int)(tile % tilesx) * kMpTX, ty0 = (int)(tile / tilesx) * kMpTY;
+        // mu_bar on the tile and its ring: grad mu and lap mu transposed
+        for (int j = tid; j < HX * HY; j += 256) {
+            const int hx = j % HX, hy = j / HX;
+            const int xv = tx0 - 1 + hx, yv = ty0 - 1 + hy;
+            if (B.wall && (yv < 0 || yv >= ny)) continue;
+            const int x = adj_wrap(xv, nx), y = B.wall ? yv : adj_wrap(yv, ny);
+            const long long k = (long long)y * nx + x;
+            const T t = tgather(B, x, y, false, [&](long long c, int i, T coef) {
+                return coef * (T(3.0 * D2Q9::w(i)) * (T(D2Q9::cx(i)) * gmx[c] + T(D2Q9::cy(i)) * gmy[c]) +
+                               T(6.0 * D2Q9::w(i)) * bl[c]);
+            });
+            const T bmu = W[B_MU][k] + t - T(10.0 / 3.0) * bl[k];
+            smu[hy][hx] = bmu;
+            if (hx >= 1 && hx <= kMpTX && hy >= 1 && hy <= kMpTY && xv < nx && yv < ny) {
+                dM += a1 * (double)W[B_ALPHA][k] + gm * (double)W[B_GL][k];
+                dS += (double)(bmu * W[A_MU1][k]);
+            }
+        }
+        __syncthreads();
+        // phi adjoint of the tile: grad phi and lap phi transposed, phi = sum g
+        const int x = tx0 + lx, y = ty0 + ly;
+        if (x < nx && y < ny) {
+            const long long k = (long long)y * nx + x;
+            const int sx0 = lx + 1, sy0 = ly + 1;
+            const T ph = W[A_PHI][k];
+            const T a = ph - K.phiA, b = ph - K.phiB, m = ph - K.phibar;
+            const T psi2 = K.beta4 * (a * b + a * m + b * m);
+            // tgather's terms in its order; mu_bar of a source centre from
+            // shared memory (the centre's tile position), its grad phi
+            // adjoint from global memory
+            auto term = [&](long long c, int hx, int hy, int i, T coef) {
+                return coef * (T(3.0 * D2Q9::w(i)) * (T(D2Q9::cx(i)) * gpx[c] + T(D2Q9::cy(i)) * gpy[c]) -
+                               K.kappa * T(6.0 * D2Q9::w(i)) * smu[hy][hx]);
+            };
+            T t = T(0);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const int cx = D2Q9::cx(i), cy = D2Q9::cy(i);
+                const int sx = B.wx(x - cx), hx = sx0 - cx;
+                int sy = y - cy;
+                if (!B.wall) {
+                    sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+                    t += term((long long)sy * nx + sx, hx, sy0 - cy, i, T(1));
+                    continue;
+                }
+                if (sy >= 0 && sy < ny) t += term((long long)sy * nx + sx, hx, sy0 - cy, i, T(1));
+                if (cy == -1 && y == 0) t += term((long long)sx, hx, sy0, i, T(1));
+                if (cy == 1 && y == ny - 1) t += term((long long)(ny - 1) * nx + sx, hx, sy0, i, T(1));
+            }
+            const T bm = smu[sy0][sx0];
+            const T bphi = W[B_PHI][k] + K.drho * W[B_RHO][k] + psi2 * bm + t + K.kappa * T(10.0 / 3.0) * bm;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) lam[(9 + i) * NS + k] += bphi;
+        }
+        __syncthreads();
     }
     adj_theta_partials(dM, dS, part);
-}
-
-// grad phi and lap phi transposed: full adjoint of phi, then phi = sum g.
-template <class T>
-__global__ void k_adj_phi(T *__restrict__ lam, const AdjP<T> P, AdjW<T> W) {
-    const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
-    const long long N = (long long)P.k.nx * P.k.ny, NS = P.k.NS;
-    const KP<T> &K = P.k;
-    const T *gx = W[B_GPHX], *gy = W[B_GPHY], *bm = W[B_MU];
-    ADJ_LOOP(k, N) {
-        const int y = row_of(k, B.nx), x = (int)(k - (long long)y * B.nx);
-        const T ph = W[A_PHI][k];
-        // psi''(phi) = 4 beta [(phi-a)(phi-b) + (phi-a)(phi-m) + (phi-b)(phi-m)]
-        const T a = ph - K.phiA, b = ph - K.phiB, m = ph - K.phibar;
-        const T psi2 = K.beta4 * (a * b + a * m + b * m);
-        const T t = tgather(B, x, y, false, [&](long long c, int i, T coef) {
-            return coef * (T(3.0 * D2Q9::w(i)) * (T(D2Q9::cx(i)) * gx[c] + T(D2Q9::cy(i)) * gy[c]) -
-                           K.kappa * T(6.0 * D2Q9::w(i)) * bm[c]);
-        });
-        const T bphi = W[B_PHI][k] + K.drho * W[B_RHO][k] + psi2 * bm[k] + t +
-                       K.kappa * T(10.0 / 3.0) * bm[k];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) lam[(9 + i) * NS + k] += bphi;
+    // the last CTA folds every CTA's partial sums
+    __threadfence();
+    if (tid == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        fold_partials<true>(part, gridDim.x, 2, acc);
+        if (tid == 0) *ticket = 0u;
     }
 }
 

@@ -512,7 +512,7 @@ lbm_status lbm_adj_work_bytes(const lbm_sim *s, size_t *bytes) {
 lbm_status lbm_adj_reset(lbm_sim *s, void *work) {
     if (lbm_status st = adj_ready(s, work)) return st;
     char *acc = static_cast<char *>(work) + lbm::adj_acc_offset(s->d.NS, s->ops->field_size);
-    LBM_CK(s, cudaMemsetAsync(acc, 0, 4 * sizeof(double), s->stream));
+    LBM_CK(s, cudaMemsetAsync(acc, 0, lbm::kAdjTicketOff + sizeof(unsigned), s->stream));
     return LBM_OK;
 }
 

@@ -101,8 +101,10 @@ struct AdjHost {
 };
 
 // Work-buffer layout of the adjoint: arrays, per-block partials, running
-// (dM, dsigma) totals and the loss.
+// (dM, dsigma) totals and the loss, then (kAdjTicketOff bytes after the
+// totals) the ticket counter of the last-CTA fold.
 constexpr int kAdjBlocks = 152 * 4;
+constexpr size_t kAdjTicketOff = 64;
 size_t adj_work_bytes(long long NS, size_t elem);
 size_t adj_part_offset(long long NS, size_t elem);
 size_t adj_acc_offset(long long NS, size_t elem);

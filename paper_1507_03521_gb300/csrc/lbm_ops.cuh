@@ -333,6 +333,11 @@ struct OpsImpl {
         return reinterpret_cast<double *>(static_cast<char *>(work) +
                                           adj_acc_offset(d.NS, sizeof(T)));
     }
+    // ticket counter of k_adj_muphi's last-CTA fold, after the totals
+    static unsigned *ticket(const Derived &d, void *work) {
+        return reinterpret_cast<unsigned *>(static_cast<char *>(work) +
+                                            adj_acc_offset(d.NS, sizeof(T)) + kAdjTicketOff);
+    }
 
     static cudaError_t adj_seed(const Derived &d, const AdjHost &h, const void *lvl,
                                 const void *target, void *lam, void *work, cudaStream_t s) {
@@ -361,9 +366,10 @@ struct OpsImpl {
             static_cast<const char *>(lvl), nullptr, make_kp<T>(d), fo);
         k_adj_collide<T><<<nb, 256, 0, s>>>(static_cast<const T *>(lam_next), L, P, W);
         k_adj_p<T><<<nb, 256, 0, s>>>(L, P, W);
-        k_adj_mu<T><<<nb, 256, 0, s>>>(P, W, part(d, work));  // also the (M, sigma) partials
-        k_adj_phi<T><<<nb, 256, 0, s>>>(L, P, W);
-        k_adj_accumulate<<<1, 256, 0, s>>>(part(d, work), nb, 2, acc(d, work));
+        // mu and phi adjoints, with the (M, sigma) sums folded by the last CTA
+        const long long tiles = (long long)((d.nx + kMpTX - 1) / kMpTX) * ((d.ny + kMpTY - 1) / kMpTY);
+        const int nt = (int)(tiles < kAdjBlocks ? tiles : kAdjBlocks);
+        k_adj_muphi<T><<<nt, 256, 0, s>>>(L, P, W, part(d, work), acc(d, work), ticket(d, work));
         return cudaGetLastError();
     }
 
