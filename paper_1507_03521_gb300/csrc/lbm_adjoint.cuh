@@ -16,9 +16,10 @@
 // from the cells whose stencils read it, with the ghost-row rules of the
 // forward step: mirror for phi and mu, linear extrapolation for p), so the
 // result is deterministic.  Kernels, in order, for one reverse step:
-//   k_step<MODE_ADJ>      the forward fields of step t, in one tile-kernel
-//                         launch (lbm_kernels.cuh),
-//   k_adj_collide         streaming and collision transposed,
+//   k_step<MODE_ADJC>     the forward fields of step t, recomputed on tiles
+//                         with halos as the forward tile step does
+//                         (lbm_kernels.cuh), then streaming and collision
+//                         transposed per cell (AdjCell, adj_collide_cell),
 //   k_adj_p               grad p transposed, then u, p, F backwards,
 //   k_adj_muphi           grad mu and lap mu transposed, then grad phi and
 //                         lap phi transposed and phi = sum g, per tile; the
@@ -51,11 +52,6 @@ enum AdjArr {
     A_COUNT
 };
 
-// The tile kernel's MODE_ADJ writes the first 16 arrays in this order.
-static_assert(A_PHI == 0 && A_RHO == 1 && A_MU == 2 && A_MU1 == 3 && A_GPHX == 4 && A_GPHY == 5 &&
-                  A_GMUX == 6 && A_GMUY == 7 && A_LMU == 8 && A_FX == 9 && A_FY == 10 && A_UX == 11 &&
-                  A_UY == 12 && A_P == 13 && A_GPX == 14 && A_GPY == 15,
-              "forward-field order of MODE_ADJ");
 
 template <class T>
 struct AdjW {
@@ -199,124 +195,143 @@ __global__ void k_adj_f1(const AdjP<T> P, AdjW<T> W) {
 
 // ------------------------------------------------------------ reverse
 
-// Streaming and collision transposed.  lam_next: lambda_{t+1}; lam: output
-// lambda_t (partial: the direct (1 - 1/tau) terms; k_adj_p and k_adj_phi
-// add the terms through p, j and phi).
-// FP32: 3 CTAs per SM (80 registers) instead of 2 at the compiler's 128
-// registers measured 7% faster over the whole backward pass at 512^2.
+// Streaming and collision transposed at cell k = (x, y), about the forward
+// fields of the step: lambda_t's direct (1 - 1/tau) terms from lam_next
+// (lambda_{t+1}; k_adj_p and k_adj_muphi add the terms through p, j and
+// phi) and the adjoints of the fields the collision reads (B_* arrays).
 template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_collide(const T *__restrict__ lam_next, T *__restrict__ lam, const AdjP<T> P,
-                              AdjW<T> W) {
-    const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
-    const long long N = (long long)P.k.nx * P.k.ny, NS = P.k.NS;
-    const KP<T> &K = P.k;
-    ADJ_LOOP(k, N) {
-        const int y = row_of(k, B.nx), x = (int)(k - (long long)y * B.nx);
-        const T phi = W[A_PHI][k], rho = W[A_RHO][k], mu = W[A_MU][k], p = W[A_P][k];
-        const T ux = W[A_UX][k], uy = W[A_UY][k], Fx = W[A_FX][k], Fy = W[A_FY][k];
-        const T grx = K.drho * W[A_GPHX][k], gry = K.drho * W[A_GPHY][k];
-        const T lm = W[A_LMU][k], gpx = W[A_GPX][k], gpy = W[A_GPY][k];
-        const T uu = ux * ux + uy * uy;
-        const T q = -T(3) * phi / rho;
-        // per-cell quotients, hoisted out of the direction loop (divisions
-        // are many instructions each; by 3 they become a multiply by 1/3)
-        const T c13 = T(1.0 / 3.0);
-        const T rho3 = rho * c13, grx3 = grx * c13, gry3 = gry * c13;
-        const T m3r = -T(3) / rho, p3r2 = T(3) * phi / (rho * rho);
-        const T Dx = gpx - Fx, Dy = gpy - Fy;
-        T bp = 0, brho = 0, bphi = 0, bmu = 0, bux = 0, buy = 0, bFx = 0, bFy = 0, bgrx = 0,
-          bgry = 0, blm = 0, bgpx = 0, bgpy = 0, balpha = 0, bgl = 0;
+__device__ __forceinline__ void adj_collide_cell(const KP<T> &K, int x, int y, long long k, T phi, T rho,
+                                                 T mu, T p, T ux, T uy, T Fx, T Fy, T gphx, T gphy,
+                                                 T lm, T gpx, T gpy, const T *__restrict__ lam_next,
+                                                 T *__restrict__ lam, const AdjW<T> &W) {
+    const Nb<T> B{K.nx, K.ny, K.wall};
+    const long long NS = K.NS;
+    const T grx = K.drho * gphx, gry = K.drho * gphy;
+    const T uu = ux * ux + uy * uy;
+    const T q = -T(3) * phi / rho;
+    // per-cell quotients, hoisted out of the direction loop (divisions
+    // are many instructions each; by 3 they become a multiply by 1/3)
+    const T c13 = T(1.0 / 3.0);
+    const T rho3 = rho * c13, grx3 = grx * c13, gry3 = gry * c13;
+    const T m3r = -T(3) / rho, p3r2 = T(3) * phi / (rho * rho);
+    const T Dx = gpx - Fx, Dy = gpy - Fy;
+    T bp = 0, brho = 0, bphi = 0, bmu = 0, bux = 0, buy = 0, bFx = 0, bFy = 0, bgrx = 0,
+      bgry = 0, blm = 0, bgpx = 0, bgpy = 0, balpha = 0, bgl = 0;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const int cx = D2Q9::cx(i), cy = D2Q9::cy(i);
-            const T w = T(D2Q9::w(i));
-            // lambda of the post-collision population: where streaming put it
-            const int yd = y + cy;
-            T lf, lg;
-            if (B.wall && (yd < 0 || yd >= B.ny)) {
-                const int o = D2Q9::opp(i);
-                lf = lam_next[o * NS + k];
-                lg = lam_next[(9 + o) * NS + k];
-                const T cuw = T(cx) * (yd < 0 ? K.uwb : K.uwt);
-                brho += -T(2) * w * cuw * lf;   // f_opp = f*_i - 2 w rho c.u_w
-                bphi += -T(6) * w * cuw * lg;   // g_opp = g*_i - 2 w phi c.u_w / cs2
-            } else {
-                const int xx = B.wx(x + cx);
-                const int yy = yd < 0 ? yd + B.ny : (yd >= B.ny ? yd - B.ny : yd);
-                const long long kd = (long long)yy * B.nx + xx;
-                lf = lam_next[i * NS + kd];
-                lg = lam_next[(9 + i) * NS + kd];
-            }
-            lam[i * NS + k] = (T(1) - K.itf) * lf;
-            lam[(9 + i) * NS + k] = (T(1) - K.itg) * lg;
-            const T beq = K.itf * lf, bF = K.pf * lf;    // d/d f^eq_i, d/d F_i
-            const T bgeq = K.itg * lg, bG = K.pg * lg;   // d/d g^eq_i, d/d G_i
-            const T cu = T(cx) * ux + T(cy) * uy;
-            const T s = T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu;
-            const T ex = T(cx) - ux, ey = T(cy) - uy;
-            T bs = 0;
-            // f^eq_i = w (p + rho s / 3)   (Eq. 24)
-            bp += w * beq;
-            brho += w * s * c13 * beq;
-            bs += w * rho3 * beq;
-            // g^eq_i = H_i + w phi s   (Eqs. 25, 27)
-            if (i == 0) {
-                bphi += bgeq;
-                bmu += -T(1.0 - D2Q9::w(0)) * K.alpha * bgeq;
-                balpha += -T(1.0 - D2Q9::w(0)) * mu * bgeq;
-            } else {
-                bmu += w * K.alpha * bgeq;
-                balpha += w * mu * bgeq;
-            }
-            bphi += w * s * bgeq;
-            bs += w * phi * bgeq;
-            // F_i = (c - u).[w (1 + s) F + w s grad rho / 3] - w rho gamma lambda lap mu / 3
-            const T eF = ex * Fx + ey * Fy, eR = ex * grx + ey * gry;
-            const T Ax = w * (T(1) + s) * Fx + w * s * grx3;
-            const T Ay = w * (T(1) + s) * Fy + w * s * gry3;
-            bFx += w * (T(1) + s) * ex * bF;
-            bFy += w * (T(1) + s) * ey * bF;
-            bgrx += w * s * c13 * ex * bF;
-            bgry += w * s * c13 * ey * bF;
-            bs += w * (eF + eR * c13) * bF;
-            bux += -Ax * bF;
-            buy += -Ay * bF;
-            brho += -w / T(3) * K.gl * lm * bF;
-            blm += -w / T(3) * rho * K.gl * bF;
-            bgl += -w / T(3) * rho * lm * bF;
-            // G_i = q w (1 + s) (c - u).(grad p - F), q = -phi / (cs2 rho)
-            const T E = ex * Dx + ey * Dy;
-            const T wg = w * (T(1) + s);
-            bphi += m3r * wg * E * bG;
-            brho += p3r2 * wg * E * bG;
-            bs += q * w * E * bG;
-            bux += -q * wg * Dx * bG;
-            buy += -q * wg * Dy * bG;
-            bgpx += q * wg * ex * bG;
-            bgpy += q * wg * ey * bG;
-            bFx += -q * wg * ex * bG;
-            bFy += -q * wg * ey * bG;
-            // s_i = 3 c.u + 4.5 (c.u)^2 - 1.5 |u|^2   (Eq. 26)
-            bux += bs * (T(3) * T(cx) + T(9) * cu * T(cx) - T(3) * ux);
-            buy += bs * (T(3) * T(cy) + T(9) * cu * T(cy) - T(3) * uy);
+    for (int i = 0; i < 9; ++i) {
+        const int cx = D2Q9::cx(i), cy = D2Q9::cy(i);
+        const T w = T(D2Q9::w(i));
+        // lambda of the post-collision population: where streaming put it
+        const int yd = y + cy;
+        T lf, lg;
+        if (B.wall && (yd < 0 || yd >= B.ny)) {
+            const int o = D2Q9::opp(i);
+            lf = lam_next[o * NS + k];
+            lg = lam_next[(9 + o) * NS + k];
+            const T cuw = T(cx) * (yd < 0 ? K.uwb : K.uwt);
+            brho += -T(2) * w * cuw * lf;   // f_opp = f*_i - 2 w rho c.u_w
+            bphi += -T(6) * w * cuw * lg;   // g_opp = g*_i - 2 w phi c.u_w / cs2
+        } else {
+            const int xx = B.wx(x + cx);
+            const int yy = yd < 0 ? yd + B.ny : (yd >= B.ny ? yd - B.ny : yd);
+            const long long kd = (long long)yy * B.nx + xx;
+            lf = lam_next[i * NS + kd];
+            lg = lam_next[(9 + i) * NS + kd];
         }
-        W[B_P][k] = bp;
-        W[B_RHO][k] = brho;
-        W[B_PHI][k] = bphi;
-        W[B_MU][k] = bmu;
-        W[B_UX][k] = bux;
-        W[B_UY][k] = buy;
-        W[B_FX][k] = bFx;
-        W[B_FY][k] = bFy;
-        W[B_GRX][k] = bgrx;
-        W[B_GRY][k] = bgry;
-        W[B_LMU][k] = blm;
-        W[B_GPX][k] = bgpx;
-        W[B_GPY][k] = bgpy;
-        W[B_ALPHA][k] = balpha;
-        W[B_GL][k] = bgl;
+        lam[i * NS + k] = (T(1) - K.itf) * lf;
+        lam[(9 + i) * NS + k] = (T(1) - K.itg) * lg;
+        const T beq = K.itf * lf, bF = K.pf * lf;    // d/d f^eq_i, d/d F_i
+        const T bgeq = K.itg * lg, bG = K.pg * lg;   // d/d g^eq_i, d/d G_i
+        const T cu = T(cx) * ux + T(cy) * uy;
+        const T s = T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu;
+        const T ex = T(cx) - ux, ey = T(cy) - uy;
+        T bs = 0;
+        // f^eq_i = w (p + rho s / 3)   (Eq. 24)
+        bp += w * beq;
+        brho += w * s * c13 * beq;
+        bs += w * rho3 * beq;
+        // g^eq_i = H_i + w phi s   (Eqs. 25, 27)
+        if (i == 0) {
+            bphi += bgeq;
+            bmu += -T(1.0 - D2Q9::w(0)) * K.alpha * bgeq;
+            balpha += -T(1.0 - D2Q9::w(0)) * mu * bgeq;
+        } else {
+            bmu += w * K.alpha * bgeq;
+            balpha += w * mu * bgeq;
+        }
+        bphi += w * s * bgeq;
+        bs += w * phi * bgeq;
+        // F_i = (c - u).[w (1 + s) F + w s grad rho / 3] - w rho gamma lambda lap mu / 3
+        const T eF = ex * Fx + ey * Fy, eR = ex * grx + ey * gry;
+        const T Ax = w * (T(1) + s) * Fx + w * s * grx3;
+        const T Ay = w * (T(1) + s) * Fy + w * s * gry3;
+        bFx += w * (T(1) + s) * ex * bF;
+        bFy += w * (T(1) + s) * ey * bF;
+        bgrx += w * s * c13 * ex * bF;
+        bgry += w * s * c13 * ey * bF;
+        bs += w * (eF + eR * c13) * bF;
+        bux += -Ax * bF;
+        buy += -Ay * bF;
+        brho += -w / T(3) * K.gl * lm * bF;
+        blm += -w / T(3) * rho * K.gl * bF;
+        bgl += -w / T(3) * rho * lm * bF;
+        // G_i = q w (1 + s) (c - u).(grad p - F), q = -phi / (cs2 rho)
+        const T E = ex * Dx + ey * Dy;
+        const T wg = w * (T(1) + s);
+        bphi += m3r * wg * E * bG;
+        brho += p3r2 * wg * E * bG;
+        bs += q * w * E * bG;
+        bux += -q * wg * Dx * bG;
+        buy += -q * wg * Dy * bG;
+        bgpx += q * wg * ex * bG;
+        bgpy += q * wg * ey * bG;
+        bFx += -q * wg * ex * bG;
+        bFy += -q * wg * ey * bG;
+        // s_i = 3 c.u + 4.5 (c.u)^2 - 1.5 |u|^2   (Eq. 26)
+        bux += bs * (T(3) * T(cx) + T(9) * cu * T(cx) - T(3) * ux);
+        buy += bs * (T(3) * T(cy) + T(9) * cu * T(cy) - T(3) * uy);
     }
+    W[B_P][k] = bp;
+    W[B_RHO][k] = brho;
+    W[B_PHI][k] = bphi;
+    W[B_MU][k] = bmu;
+    W[B_UX][k] = bux;
+    W[B_UY][k] = buy;
+    W[B_FX][k] = bFx;
+    W[B_FY][k] = bFy;
+    W[B_GRX][k] = bgrx;
+    W[B_GRY][k] = bgry;
+    W[B_LMU][k] = blm;
+    W[B_GPX][k] = bgpx;
+    W[B_GPY][k] = bgpy;
+    W[B_ALPHA][k] = balpha;
+    W[B_GL][k] = bgl;
 }
+
+// MODE_ADJC of the tile kernel (k_step): per owned cell, the forward fields
+// the later reverse kernels read (k_adj_p: phi, rho, lap mu, u, grad phi,
+// grad mu; k_adj_muphi: phi, mu per unit sigma), then the collision
+// adjoint about all of them, in the same thread.
+template <class T>
+struct AdjCell {
+    static __device__ __forceinline__ void run(const KP<T> &K, const FieldOut<T> &out, int x, int y,
+                                               long long k, const Macro<T> &m, T mu1, T p, T gpx,
+                                               T gpy) {
+        const AdjW<T> W{out.adj, out.adj_ns};
+        W[A_PHI][k] = m.phi;
+        W[A_RHO][k] = m.rho;
+        W[A_MU1][k] = mu1;
+        W[A_GPHX][k] = m.gphx;
+        W[A_GPHY][k] = m.gphy;
+        W[A_GMUX][k] = m.gmux;
+        W[A_GMUY][k] = m.gmuy;
+        W[A_LMU][k] = m.lmu;
+        W[A_UX][k] = m.ux;
+        W[A_UY][k] = m.uy;
+        adj_collide_cell(K, x, y, k, m.phi, m.rho, m.mu, p, m.ux, m.uy, m.Fx, m.Fy, m.gphx, m.gphy,
+                         m.lmu, gpx, gpy, out.lam_next, out.lam, W);
+    }
+};
 
 // grad p transposed (extrapolated ghosts) gives the full adjoint of p; then
 // p, u, F backwards (Eqs. 31-32) and the f terms through sum f and j.

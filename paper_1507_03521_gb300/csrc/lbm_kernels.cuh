@@ -54,11 +54,11 @@ static_assert(D2Q9::opp(1) == 3 && D2Q9::opp(2) == 4 && D2Q9::opp(3) == 1 && D2Q
 static_assert(D2Q9::opp(5) == 7 && D2Q9::opp(6) == 8 && D2Q9::opp(7) == 5 && D2Q9::opp(8) == 6,
               "opposite of diagonal directions");
 
-// MODE_ADJ: the forward fields that the adjoint of the step linearises
-// about, written to out.adj (16 arrays, stride out.adj_ns, in this order:
-// phi, rho, mu, mu per unit sigma, grad phi (x, y), grad mu (x, y), lap mu,
-// F (x, y), u (x, y), p, grad p (x, y)).
-enum { MODE_STEP = 0, MODE_FIELDS = 1, MODE_ADJ = 2 };
+// MODE_ADJC: the reverse step's first kernel: per cell, the forward fields
+// that the adjoint of the step linearises about and the later reverse
+// kernels read, then the streaming and collision adjoint about them
+// (AdjCell, lbm_adjoint.cuh).
+enum { MODE_STEP = 0, MODE_FIELDS = 1, MODE_ADJC = 3 };
 
 // Kernel parameters, converted once to the compute type T on the host.
 template <class T>
@@ -104,12 +104,18 @@ __device__ __forceinline__ bool dbg_ok(unsigned *w, bool ok, unsigned code) {
 template <class T>
 struct FieldOut {
     T *phi, *rho, *p, *ux, *uy, *mu, *P;
-    // MODE_ADJ: base of the 16 field arrays, their stride, and 4 beta and
-    // kappa per unit sigma (for mu per unit sigma)
+    // MODE_ADJC: base of the adjoint's field arrays (AdjArr), their stride,
+    // and 4 beta and kappa per unit sigma (for mu per unit sigma)
     T *adj = nullptr;
     long long adj_ns = 0;
     T beta1x4 = T(0), kappa1 = T(0);
+    // MODE_ADJC: lambda_{t+1} (read) and lambda_t (written)
+    const T *lam_next = nullptr;
+    T *lam = nullptr;
 };
+
+template <class T>
+struct AdjCell;  // MODE_ADJC's per-cell work, defined in lbm_adjoint.cuh
 
 // ------------------------------------------------------------ storage
 
@@ -465,8 +471,12 @@ __device__ __forceinline__ Macro<T> macro_at(const Tile<T, TY> &s, const KP<T> &
 
 // -------------------------------------------------------------- kernels
 
+
 template <class T, class ST, int RPT, int MODE>
-__global__ void __launch_bounds__(256)
+// MODE_ADJC in FP32 is held to 3 CTAs per SM (80 registers, 24 B spilled):
+// at the compiler's 174 registers (1 CTA per SM) the adjoint's backward
+// pass at 512^2 took 0.46 s, at 128 (2 CTAs) 0.376 s, at 80 0.370-0.374 s.
+__global__ void __launch_bounds__(256, (MODE == MODE_ADJC && sizeof(T) == 4) ? 3 : 1)
 k_step(const char *__restrict__ src, char *__restrict__ dst, const KP<T> P, FieldOut<T> out) {
     constexpr int TY = 8 * RPT;
     using TL = Tile<T, TY>;
@@ -568,27 +578,10 @@ k_step(const char *__restrict__ src, char *__restrict__ dst, const KP<T> P, Fiel
         grad9(s.p, TL::iq(ly, lx), TL::QW, gpx, gpy);
         const long long k = (long long)gy * nx + gx;
         const T pc = s.p[TL::iq(ly, lx)];
-        if (MODE == MODE_ADJ) {
-            T *a = out.adj + k;
-            const long long S = out.adj_ns;
+        if constexpr (MODE == MODE_ADJC) {
             const T q = (m.phi - P.phiA) * (m.phi - P.phiB) * (m.phi - P.phibar);
             const T lph = lap9(s.phi, TL::ip(ly, lx), TL::PW);
-            a[0 * S] = m.phi;
-            a[1 * S] = m.rho;
-            a[2 * S] = m.mu;
-            a[3 * S] = out.beta1x4 * q - out.kappa1 * lph;
-            a[4 * S] = m.gphx;
-            a[5 * S] = m.gphy;
-            a[6 * S] = m.gmux;
-            a[7 * S] = m.gmuy;
-            a[8 * S] = m.lmu;
-            a[9 * S] = m.Fx;
-            a[10 * S] = m.Fy;
-            a[11 * S] = m.ux;
-            a[12 * S] = m.uy;
-            a[13 * S] = pc;
-            a[14 * S] = gpx;
-            a[15 * S] = gpy;
+            AdjCell<T>::run(P, out, gx, gy, k, m, out.beta1x4 * q - out.kappa1 * lph, pc, gpx, gpy);
             continue;
         }
         if (MODE == MODE_FIELDS) {

@@ -354,17 +354,19 @@ struct OpsImpl {
         const AdjW<T> W = make_w(d, work);
         const int nb = adj_grid(d);
         T *L = static_cast<T *>(lam);
-        // the forward fields of step t, in one tile-kernel launch
-        cudaError_t e = prepare<MODE_ADJ>();
+        // the forward fields of step t and the collision adjoint, in one
+        // tile-kernel launch
+        cudaError_t e = prepare<MODE_ADJC>();
         if (e != cudaSuccess) return e;
         FieldOut<T> fo{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
         fo.adj = W.a;
         fo.adj_ns = d.NS;
         fo.beta1x4 = T(4) * P.beta1;
         fo.kappa1 = P.kappa1;
-        k_step<T, ST, RPT, MODE_ADJ><<<grid(d), dim3(32, 8), TL::bytes, s>>>(
+        fo.lam_next = static_cast<const T *>(lam_next);
+        fo.lam = L;
+        k_step<T, ST, RPT, MODE_ADJC><<<grid(d), dim3(32, 8), TL::bytes, s>>>(
             static_cast<const char *>(lvl), nullptr, make_kp<T>(d), fo);
-        k_adj_collide<T><<<nb, 256, 0, s>>>(static_cast<const T *>(lam_next), L, P, W);
         k_adj_p<T><<<nb, 256, 0, s>>>(L, P, W);
         // mu and phi adjoints, with the (M, sigma) sums folded by the last CTA
         const long long tiles = (long long)((d.nx + kMpTX - 1) / kMpTX) * ((d.ny + kMpTY - 1) / kMpTY);
