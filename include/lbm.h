@@ -263,6 +263,36 @@ LBM_API lbm_status lbm_adj_segment(lbm_sim *sim, int64_t n, void *states, size_t
                                    void *lam, void *lam_tmp, void *work);
 LBM_API lbm_status lbm_adj_set_graph(lbm_sim *sim, int on);
 
+/* The same sweep with the recompute of each segment overlapped with the
+ * reverse steps of the one after it, for a caller that alternates two
+ * state buffers of K levels:
+ *   lbm_adj_recompute        levels 1 .. n-1 of `states` from level 0 (the
+ *                            recompute half of lbm_adj_segment), on the
+ *                            handle's stream;
+ *   lbm_adj_reverse_overlap  the n reverse steps of `states` (levels 0 ..
+ *                            n-1 already recomputed; lam, lam_tmp, work as
+ *                            lbm_adj_segment) on the handle's stream, while
+ *                            a second stream recomputes levels 1 .. n_next-1
+ *                            of `next_states` (a different buffer, same
+ *                            stride) from its level 0, which the caller has
+ *                            filled with the next segment's checkpoint by
+ *                            work issued before this call on the handle's
+ *                            stream.  n_next = 0 (or 1): nothing to
+ *                            recompute.  Work issued after the call on the
+ *                            handle's stream runs after both halves.
+ * Per segment the results equal lbm_adj_segment's bit for bit.  The second
+ * stream and its two events are created on the current device by the first
+ * call with n_next > 1 and live as long as the handle.  With
+ * lbm_adj_set_graph(sim, 1) each call is captured as one CUDA graph (both
+ * streams) and replayed by later calls with the same sizes and buffers; the
+ * graphs of the last two distinct calls are kept.  Errors: as
+ * lbm_adj_segment (for both buffers), plus LBM_ERR_ARG for n_next < 0 or
+ * next_states == states. */
+LBM_API lbm_status lbm_adj_recompute(lbm_sim *sim, int64_t n, void *states, size_t level_stride);
+LBM_API lbm_status lbm_adj_reverse_overlap(lbm_sim *sim, int64_t n, void *states,
+                                           size_t level_stride, void *lam, void *lam_tmp,
+                                           void *work, int64_t n_next, void *next_states);
+
 /* ------------------------------------------------------------------ batches
  * The batched form: n independent domains, each with its own size and
  * parameters (one dtype for the whole batch; every nx a multiple of 8; not

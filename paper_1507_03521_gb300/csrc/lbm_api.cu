@@ -168,9 +168,26 @@ struct lbm_sim {
     int64_t adj_n = -1;
     size_t adj_stride = 0;
     const void *adj_key[4] = {nullptr, nullptr, nullptr, nullptr};
+    // overlapped reverse sweep (lbm_adj_reverse_overlap): the second stream
+    // that recomputes the next segment, fork/join events, and the graphs of
+    // the last two calls (a sweep alternates two state buffers)
+    cudaStream_t adj_side = nullptr;
+    cudaEvent_t adj_fork = nullptr, adj_join = nullptr;
+    struct OvGraph {
+        cudaGraphExec_t exec = nullptr;
+        int64_t n = -1, n_next = -1;
+        size_t stride = 0;
+        const void *key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    } adj_ov[2];
+    int adj_ov_next = 0;  // entry the next capture replaces
 
     ~lbm_sim() {
         if (adj_exec) cudaGraphExecDestroy(adj_exec);
+        for (auto &g : adj_ov)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (adj_fork) cudaEventDestroy(adj_fork);
+        if (adj_join) cudaEventDestroy(adj_join);
+        if (adj_side) cudaStreamDestroy(adj_side);
     }
 
     char *level(int i) { return state + (size_t)i * L.level; }
@@ -562,25 +579,30 @@ lbm_status lbm_adj_set_graph(lbm_sim *s, int on) {
     return LBM_OK;
 }
 
-// The launch sequence of one segment: n - 1 forward steps that fill levels
-// 1 .. n-1 of `states` from level 0, then n reverse steps from the last
-// level down, alternating between lam and lam_tmp so that lambda_{t0}
-// lands in lam.
-static cudaError_t adj_segment_issue(lbm_sim *s, int64_t n, char *states, size_t lb, void *lam,
-                                     void *lam_tmp, void *work) {
+// The recompute of one segment on stream st: n - 1 forward steps that fill
+// levels 1 .. n-1 of `states` from level 0.  It runs the kernel lbm_step
+// runs: where the handle's levels have tensor maps (FP32), each source level
+// of the segment gets one too.
+static cudaError_t adj_recompute_issue(lbm_sim *s, int64_t n, char *states, size_t lb,
+                                       cudaStream_t st) {
     const Ops *o = s->ops;
-    // The recompute runs the kernel lbm_step runs: where the handle's
-    // levels have tensor maps (FP32), each source level of the segment gets
-    // one too.
     Derived dk = s->d;
     for (int64_t k = 1; k < n; ++k) {
         char *src = states + (k - 1) * lb;
         dk.tm_base[0] = dk.tm_base[1] = nullptr;
         if (s->d.tm_base[0] && encode_level_map(&dk.tm[0], src, dk, o->tma_box)) dk.tm_base[0] = src;
-        cudaError_t e = o->step(dk, src, states + k * lb, s->stream);
+        cudaError_t e = o->step(dk, src, states + k * lb, st);
         if (e != cudaSuccess) return e;
     }
-    const size_t sb = level_state_bytes(s->d, o);
+    return cudaSuccess;
+}
+
+// The n reverse steps of one segment on the handle's stream, from the last
+// level down, alternating between lam and lam_tmp so that lambda_{t0} lands
+// in lam.
+static cudaError_t adj_reverse_issue(lbm_sim *s, int64_t n, char *states, size_t lb, void *lam,
+                                     void *lam_tmp, void *work) {
+    const size_t sb = level_state_bytes(s->d, s->ops);
     void *in = lam, *out = lam_tmp;
     if (n % 2 == 1) {  // an odd count ends in lam only if it starts from lam_tmp
         cudaError_t e = cudaMemcpyAsync(lam_tmp, lam, sb, cudaMemcpyDeviceToDevice, s->stream);
@@ -590,13 +612,42 @@ static cudaError_t adj_segment_issue(lbm_sim *s, int64_t n, char *states, size_t
     }
     const lbm::AdjHost h = adj_host(s->prm);
     for (int64_t k = n - 1; k >= 0; --k) {
-        cudaError_t e = o->adj_step(s->d, h, states + k * lb, in, out, work, s->stream);
+        cudaError_t e = s->ops->adj_step(s->d, h, states + k * lb, in, out, work, s->stream);
         if (e != cudaSuccess) return e;
         void *t = in;
         in = out;
         out = t;
     }
     return cudaSuccess;
+}
+
+// The launch sequence of one segment: its recompute, then its reverse steps.
+static cudaError_t adj_segment_issue(lbm_sim *s, int64_t n, char *states, size_t lb, void *lam,
+                                     void *lam_tmp, void *work) {
+    cudaError_t e = adj_recompute_issue(s, n, states, lb, s->stream);
+    return e != cudaSuccess ? e : adj_reverse_issue(s, n, states, lb, lam, lam_tmp, work);
+}
+
+// The overlapped pair: the recompute of the next segment on the side stream
+// (forked after everything issued so far on the handle's stream, so after
+// the caller's copy of its checkpoint) and the reverse steps of this one on
+// the handle's stream, joined at the end.
+static cudaError_t adj_overlap_issue(lbm_sim *s, int64_t n, char *states, size_t lb, void *lam,
+                                     void *lam_tmp, void *work, int64_t n_next, char *next_states) {
+    cudaError_t e = cudaSuccess;
+    if (n_next > 1) {
+        if ((e = cudaEventRecord(s->adj_fork, s->stream)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s->adj_side, s->adj_fork, 0)) != cudaSuccess) return e;
+        if ((e = adj_recompute_issue(s, n_next, next_states, lb, s->adj_side)) != cudaSuccess) return e;
+    }
+    e = adj_reverse_issue(s, n, states, lb, lam, lam_tmp, work);
+    if (n_next > 1) {
+        // join even after a failed issue, so that no capture is left forked
+        const cudaError_t e1 = cudaEventRecord(s->adj_join, s->adj_side);
+        const cudaError_t e2 = cudaStreamWaitEvent(s->stream, s->adj_join, 0);
+        if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+    }
+    return e;
 }
 
 lbm_status lbm_adj_segment(lbm_sim *s, int64_t n, void *states, size_t level_stride, void *lam,
@@ -642,6 +693,87 @@ lbm_status lbm_adj_segment(lbm_sim *s, int64_t n, void *states, size_t level_str
         for (int i = 0; i < 4; ++i) s->adj_key[i] = key[i];
     }
     LBM_CK(s, cudaGraphLaunch(s->adj_exec, s->stream));
+    return LBM_OK;
+}
+
+static lbm_status adj_states_ok(lbm_sim *s, const void *states, size_t level_stride) {
+    const size_t sb = level_state_bytes(s->d, s->ops);
+    if (!states) return s->fail(LBM_ERR_ARG, "null pointer");
+    if (level_stride < sb || (level_stride & 255) || (reinterpret_cast<uintptr_t>(states) & 255))
+        return s->fail(LBM_ERR_ARG, "level_stride must be >= lbm_state_bytes and states and "
+                                    "level_stride 256-byte aligned");
+    return LBM_OK;
+}
+
+lbm_status lbm_adj_recompute(lbm_sim *s, int64_t n, void *states, size_t level_stride) {
+    lbm::NvtxRange r_call("lbm_adj_recompute");
+    if (!s) return LBM_ERR_ARG;
+    if (!s->ops->adj_step || s->d.lag) return s->fail(LBM_ERR_ARG, "no adjoint for this handle");
+    if (n < 1) return s->fail(LBM_ERR_ARG, "a segment needs at least one step");
+    if (lbm_status st = adj_states_ok(s, states, level_stride)) return st;
+    LBM_CK(s, adj_recompute_issue(s, n, static_cast<char *>(states), level_stride, s->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_adj_reverse_overlap(lbm_sim *s, int64_t n, void *states, size_t level_stride,
+                                   void *lam, void *lam_tmp, void *work, int64_t n_next,
+                                   void *next_states) {
+    lbm::NvtxRange r_call("lbm_adj_reverse_overlap");
+    if (lbm_status st = adj_ready(s, work)) return st;
+    if (!lam || !lam_tmp) return s->fail(LBM_ERR_ARG, "null pointer");
+    if (lam == lam_tmp) return s->fail(LBM_ERR_ARG, "lam and lam_tmp must differ");
+    if (n < 1 || n_next < 0) return s->fail(LBM_ERR_ARG, "n >= 1 and n_next >= 0 required");
+    if (lbm_status st = adj_states_ok(s, states, level_stride)) return st;
+    if (n_next > 0) {
+        if (lbm_status st = adj_states_ok(s, next_states, level_stride)) return st;
+        if (next_states == states) return s->fail(LBM_ERR_ARG, "states and next_states must differ");
+    }
+    if (n_next > 1 && !s->adj_side) {
+        LBM_CK(s, cudaStreamCreateWithFlags(&s->adj_side, cudaStreamNonBlocking));
+        LBM_CK(s, cudaEventCreateWithFlags(&s->adj_fork, cudaEventDisableTiming));
+        LBM_CK(s, cudaEventCreateWithFlags(&s->adj_join, cudaEventDisableTiming));
+    }
+    char *st_base = static_cast<char *>(states);
+    char *nx_base = static_cast<char *>(next_states);
+    if (!s->adj_graph) {
+        LBM_CK(s, adj_overlap_issue(s, n, st_base, level_stride, lam, lam_tmp, work, n_next, nx_base));
+        return LBM_OK;
+    }
+    const void *key[5] = {states, next_states, lam, lam_tmp, work};
+    lbm_sim::OvGraph *hit = nullptr;
+    for (auto &g : s->adj_ov) {
+        bool same = g.exec && g.n == n && g.n_next == n_next && g.stride == level_stride;
+        for (int i = 0; i < 5 && same; ++i) same = g.key[i] == key[i];
+        if (same) hit = &g;
+    }
+    if (!hit) {
+        hit = &s->adj_ov[s->adj_ov_next];
+        s->adj_ov_next = 1 - s->adj_ov_next;
+        if (hit->exec) {
+            cudaGraphExecDestroy(hit->exec);
+            hit->exec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        LBM_CK(s, cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t ei =
+            adj_overlap_issue(s, n, st_base, level_stride, lam, lam_tmp, work, n_next, nx_base);
+        const cudaError_t ec = cudaStreamEndCapture(s->stream, &g);
+        if (ei != cudaSuccess || ec != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return s->cuda(ei != cudaSuccess ? ei : ec, "capture of an overlapped adjoint segment");
+        }
+        const cudaError_t eg = cudaGraphInstantiate(&hit->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (eg != cudaSuccess) {
+            hit->exec = nullptr;
+            return s->cuda(eg, "instantiation of an overlapped adjoint segment graph");
+        }
+        hit->n = n;
+        hit->n_next = n_next;
+        hit->stride = level_stride;
+        for (int i = 0; i < 5; ++i) hit->key[i] = key[i];
+    }
+    LBM_CK(s, cudaGraphLaunch(hit->exec, s->stream));
     return LBM_OK;
 }
 

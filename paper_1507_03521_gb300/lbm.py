@@ -35,6 +35,7 @@ EXPORTS = ["lbm_version", "lbm_buffer_sizes", "lbm_create", "lbm_bind_buffers", 
            "lbm_batch_step_count", "lbm_batch_segment", "lbm_batch_work_items", "lbm_batch_last_error",
            "lbm_batch_destroy", "lbm_adj_work_bytes", "lbm_adj_reset", "lbm_adj_seed",
            "lbm_adj_step", "lbm_adj_init", "lbm_adj_grads", "lbm_adj_segment", "lbm_adj_set_graph",
+           "lbm_adj_recompute", "lbm_adj_reverse_overlap",
            "lbm_slabs_buffer_sizes", "lbm_slabs_create", "lbm_slabs_bind_buffers",
            "lbm_slabs_scatter", "lbm_slabs_gather", "lbm_slabs_step", "lbm_slabs_rows",
            "lbm_slabs_step_count", "lbm_slabs_last_error", "lbm_slabs_destroy",
@@ -226,6 +227,11 @@ def _open(path: str):
     lib.lbm_adj_segment.argtypes = [_vp, ctypes.c_int64, _vp, ctypes.c_size_t, _vp, _vp, _vp]
     lib.lbm_adj_set_graph.restype = S
     lib.lbm_adj_set_graph.argtypes = [_vp, ctypes.c_int]
+    lib.lbm_adj_recompute.restype = S
+    lib.lbm_adj_recompute.argtypes = [_vp, ctypes.c_int64, _vp, ctypes.c_size_t]
+    lib.lbm_adj_reverse_overlap.restype = S
+    lib.lbm_adj_reverse_overlap.argtypes = [_vp, ctypes.c_int64, _vp, ctypes.c_size_t, _vp, _vp, _vp,
+                                            ctypes.c_int64, _vp]
     lib.lbm_test_unfinished_tiles.restype = S
     lib.lbm_test_unfinished_tiles.argtypes = [_vp, ctypes.c_int]
     return lib
@@ -420,6 +426,20 @@ class Sim:
         lambda_{t0}."""
         self._check(self._lib.lbm_adj_segment(self._h, int(n), states.data_ptr(), int(level_stride),
                                               lam.data_ptr(), lam_tmp.data_ptr(), work.data_ptr()))
+
+    def adj_recompute(self, n, states, level_stride):
+        """Levels 1 .. n-1 of `states` from level 0 (lbm_adj_recompute)."""
+        self._check(self._lib.lbm_adj_recompute(self._h, int(n), states.data_ptr(), int(level_stride)))
+
+    def adj_reverse_overlap(self, n, states, level_stride, lam, lam_tmp, work, n_next=0,
+                            next_states=None):
+        """n reverse steps of `states` (already recomputed) while a second
+        stream recomputes n_next levels of `next_states` from its level 0
+        (lbm_adj_reverse_overlap)."""
+        nxt = next_states.data_ptr() if next_states is not None else None
+        self._check(self._lib.lbm_adj_reverse_overlap(
+            self._h, int(n), states.data_ptr(), int(level_stride), lam.data_ptr(), lam_tmp.data_ptr(),
+            work.data_ptr(), int(n_next), nxt))
 
     def test_unfinished_tiles(self, on: bool):
         """Test hook: tile loads that never finish, so their bounded waits

@@ -225,3 +225,86 @@ def test_segment_call_equals_step_by_step(L, dtype, graph):
             assert b.adj_grads(w) == ref_g[i], (i, n)
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("graph", [False, True])
+def test_overlapped_sweep_equals_segment_sweep(L, dtype, graph):
+    """lbm_adj_recompute + lbm_adj_reverse_overlap (each segment's reverse
+    steps while a second stream recomputes the next segment into the other
+    state buffer) give bit for bit the lambda and (M, sigma) totals of one
+    lbm_adj_segment call per segment, over a sweep of three segments of
+    odd and even length, twice in a row (graph replay of both buffer
+    orders)."""
+    p, phi, ux, uy = W.small_case(48, 37, seed=35, walls=True, gravity=1e-5, u_wall=0.01)
+    stream = torch.cuda.Stream()
+    lens = (5, 4, 5)
+    with torch.cuda.stream(stream):
+        a = L.Sim(p, dtype, stream=stream)
+        a.init_phi(phi, ux, uy)
+        a.step(2)
+        ckpts = []
+        for n in lens:
+            ckpts.append(a.get_state()[0])
+            a.step(n)
+        sb = a.state_bytes()
+        stride = (sb + 255) // 256 * 256
+        rng = np.random.default_rng(11)
+        elem = 8 if dtype == "f64" else 4
+        lam0 = torch.from_numpy(rng.standard_normal(sb // elem).astype(
+            np.float64 if dtype == "f64" else np.float32)).view(torch.uint8).to(ckpts[0].device)
+        N = p["nx"] * p["ny"]
+        npdt = np.float64 if dtype == "f64" else np.float32
+        dev = ckpts[0].device
+
+        def sweep(overlap, sim, w):
+            lam = lam0.clone()
+            tmp = torch.empty_like(lam)
+            A = torch.empty(max(lens) * stride, dtype=torch.uint8, device=dev)
+            if not overlap:
+                for s in reversed(range(len(lens))):
+                    A[:sb].copy_(ckpts[s])
+                    sim.adj_segment(lens[s], A, stride, lam, tmp, w)
+                return lam
+            B = torch.empty_like(A)
+            cur, nxt = A, B
+            cur[:sb].copy_(ckpts[-1])
+            sim.adj_recompute(lens[-1], cur, stride)
+            for s in reversed(range(len(lens))):
+                n_next = lens[s - 1] if s > 0 else 0
+                if n_next:
+                    nxt[:sb].copy_(ckpts[s - 1])
+                sim.adj_reverse_overlap(lens[s], cur, stride, lam, tmp, w, n_next, nxt)
+                cur, nxt = nxt, cur
+            return lam
+
+        b = L.Sim(p, dtype, stream=stream)
+        b.init_phi(phi, ux, uy)
+        b.adj_set_graph(graph)
+        for rep in range(2):
+            w_ref, w = a.adj_work(), b.adj_work()
+            ref = sweep(False, a, w_ref)
+            got = sweep(True, b, w)
+            assert np.array_equal(_state_pops(got, N, npdt), _state_pops(ref, N, npdt)), rep
+            assert b.adj_grads(w) == a.adj_grads(w_ref), rep
+        a.close()
+        b.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_rollout_overlap_does_not_change_gradients(L, dtype):
+    """The autograd wrapper's overlapped backward (two state buffers) and
+    its one-call-per-segment backward give identical gradients, with a last
+    segment shorter than K."""
+    from paper_1507_03521_gb300.adjoint import rollout_loss
+    p, phi = W.shear_droplet(n=32, R=6.0)
+    tgt = torch.from_numpy(np.roll(phi, 1, axis=0))
+    res = []
+    for overlap in (False, True):
+        ph = torch.from_numpy(phi).clone().requires_grad_(True)
+        M = torch.tensor(p["M"], dtype=torch.float64, requires_grad=True)
+        sg = torch.tensor(p["sigma"], dtype=torch.float64, requires_grad=True)
+        rollout_loss(ph, M, sg, p, 45, tgt, K=7, dtype=dtype, overlap=overlap).backward()
+        res.append((ph.grad.numpy().copy(), M.grad.item(), sg.grad.item()))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert res[0][1] == res[1][1] and res[0][2] == res[1][2]
