@@ -478,10 +478,9 @@ LBM_API void lbm3_destroy(lbm3_sim *s);
  * grids return LBM_ERR_NOMEM without touching the GPU.  LBM_ERR_ARG for
  * invalid parameters or a NULL level, LBM_ERR_NONFINITE for NaN/Inf sums,
  * LBM_ERR_CUDA for a failed CUDA call; lbm_create_error() gives the
- * message.  The first call on each device looks up the scratch array's
- * device address (cudaGetSymbolAddress) and keeps it for the process; make
- * that first call before any stream capture, and make no call on a device
- * after a cudaDeviceReset of it.  All calls in the process share the one scratch array,
+ * message.  Every call looks up the scratch array's device address on the
+ * current device (cudaGetSymbolAddress) and synchronises `stream`, so it
+ * cannot be part of a stream capture.  All calls in the process share the one scratch array,
  * which keeps the last call's contents (each call writes every slot it
  * reads, so nothing needs clearing): calls that overlap on the GPU, from
  * any thread or stream, race with each other. */

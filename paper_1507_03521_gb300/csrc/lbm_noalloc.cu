@@ -13,7 +13,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 
 #include "lbm.h"
 #include "lbm_internal.h"
@@ -91,30 +90,18 @@ __global__ void k_mass_noalloc_final(int nblocks, double *__restrict__ scratch) 
 
 // Device address of g_mass_scratch for the current device.  In host code
 // the name g_mass_scratch is only a host-side stand-in, not a device
-// address, so it is looked up with cudaGetSymbolAddress once per device
-// (with that device current) and cached.  The cache outlives a
-// cudaDeviceReset, after which the library is not to be used on that
-// device again.
-std::mutex g_scratch_mu;
-double *g_scratch_dev[64] = {};
-
+// address, so it is looked up with cudaGetSymbolAddress, on every call: the
+// lookup is cheap next to the two launches and the synchronisation, and a
+// cached address would go stale if the module were reloaded (after a
+// cudaDeviceReset).
 lbm_status scratch_address(double **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
-        lbm_internal_set_error("lbm_mass_noalloc: no usable current CUDA device");
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_mass_scratch);
+    if (e != cudaSuccess || !p) {
+        lbm_internal_set_error("lbm_mass_noalloc: cudaGetSymbolAddress failed");
         return LBM_ERR_CUDA;
     }
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_dev[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_mass_scratch);
-        if (e != cudaSuccess || !p) {
-            lbm_internal_set_error("lbm_mass_noalloc: cudaGetSymbolAddress failed");
-            return LBM_ERR_CUDA;
-        }
-        g_scratch_dev[dev] = static_cast<double *>(p);
-    }
-    *out = g_scratch_dev[dev];
+    *out = static_cast<double *>(p);
     return LBM_OK;
 }
 
