@@ -230,10 +230,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // swizzle, zero fill outside (never read: only strips whose rows lie inside
 // the level use the map).  False when the map cannot be made; the strip
 // kernel then copies by chunks.
-static bool encode_level_map(CUtensorMap *m, const void *lvl, const Derived &d, int box) {
+namespace lbm {
+bool encode_level_map(CUtensorMap *m, const void *lvl, const Derived &d, int box) {
     const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc || box <= 0 || box > 256) return false;
-    cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, 18};
+    // rows a level holds: the domain's, or a y-slab's own rows and ghosts
+    const int rows = d.slab ? d.rows : d.ny;
+    cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)rows, 18};
     cuuint64_t strides[2] = {(cuuint64_t)d.nx * 4, (cuuint64_t)d.NS * 4};
     cuuint32_t boxd[3] = {(cuuint32_t)box, 1, 9};
     cuuint32_t estr[3] = {1, 1, 1};
@@ -242,6 +245,8 @@ static bool encode_level_map(CUtensorMap *m, const void *lvl, const Derived &d, 
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+}  // namespace lbm
+using lbm::encode_level_map;
 
 // The kernels' error word: bit 0, a bounded wait for a tile load ran out.
 static lbm_status error_word(lbm_sim *s) {

@@ -92,6 +92,11 @@ struct Derived {
     double grav, rhoref, tau_f, tau_g, uwb, uwt;
 };
 
+// The 3-D tensor map (x, row, slot) of one FP32 level of d (a whole domain
+// or a y-slab), with boxes of `box` columns x 1 row x 9 slots; false where
+// the driver entry point is missing or the level cannot be described.
+bool encode_level_map(CUtensorMap *m, const void *lvl, const Derived &d, int box);
+
 // Extra constants of the adjoint: derivatives of the model constants with
 // respect to M and sigma.
 struct AdjHost {

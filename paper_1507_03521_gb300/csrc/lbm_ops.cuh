@@ -123,14 +123,14 @@ struct OpsImpl {
         if constexpr (kDev && SLAB) return cudaErrorNotSupported;
         else return strip_step_impl<SLAB>(d, src, dst, s);
     }
-    // tensor-tile staging: FP32 single domains whose rows are 128-byte
-    // aligned row buffers (the 120-column strips)
+    // tensor-tile staging: FP32 single domains and y-slabs whose rows are
+    // 128-byte aligned row buffers (the 120-column strips)
     static constexpr bool kTma = std::is_same<ST, PlainStore<float>>::value && SM::TMA_ROWS;
 
     template <bool SLAB>
     static cudaError_t strip_step_impl(const Derived &d, const void *src, void *dst, cudaStream_t s) {
-        if constexpr (kTma && !SLAB) {
-            if (const CUtensorMap *m = d.map_for(src)) return strip_step_tma(d, src, dst, *m, s);
+        if constexpr (kTma) {
+            if (const CUtensorMap *m = d.map_for(src)) return strip_step_tma<SLAB>(d, src, dst, *m, s);
         }
         dim3 grid;
         int seg_h = 0;
@@ -141,18 +141,19 @@ struct OpsImpl {
         return cudaGetLastError();
     }
 
+    template <bool SLAB>
     static cudaError_t strip_step_tma(const Derived &d, const void *src, void *dst,
                                       const CUtensorMap &m, cudaStream_t s) {
         static PerDevice<StripCfg> cfg;
         StripCfg c;
         cudaError_t e = cfg.get(c, [](int dev, StripCfg &v) {
-            return strip_cfg(k_strip_tma<T, ST, SW, DEPTH>, (int)SM::bytes_tma, dev, v);
+            return strip_cfg(k_strip_tma<T, ST, SW, DEPTH, SLAB>, (int)SM::bytes_tma, dev, v);
         });
         if (e != cudaSuccess) return e;
         dim3 grid;
         int seg_h = 0;
         one_wave(d, c, grid, seg_h);
-        k_strip_tma<T, ST, SW, DEPTH><<<grid, NT, SM::bytes_tma, s>>>(
+        k_strip_tma<T, ST, SW, DEPTH, SLAB><<<grid, NT, SM::bytes_tma, s>>>(
             static_cast<const char *>(src), static_cast<char *>(dst), make_kp<T>(d), seg_h, m);
         return cudaGetLastError();
     }

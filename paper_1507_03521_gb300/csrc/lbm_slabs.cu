@@ -244,6 +244,18 @@ lbm_status lbm_slabs_bind_buffers(lbm_slabs *s, void *state, size_t state_bytes,
     char *const st_base = static_cast<char *>(state);
     const lbm_status bound = bind_tables(s, st_base, work);
     s->state = bound == LBM_OK ? st_base : nullptr;
+    // tensor maps of every slab's two levels (FP32): the slab steps take
+    // their interior strips' rows as tensor tiles; a level without a map
+    // is stepped with chunk copies
+    for (int i = 0; i < n && bound == LBM_OK; ++i) {
+        Derived &d = s->P.ds[i];
+        for (int lv = 0; lv < 2; ++lv) {
+            d.tm_base[lv] = nullptr;
+            if (s->ops->tma_box > 0 &&
+                lbm::encode_level_map(&d.tm[lv], s->level(i, lv), d, s->ops->tma_box))
+                d.tm_base[lv] = s->level(i, lv);
+        }
+    }
     return bound;
 }
 

@@ -1036,16 +1036,16 @@ k_strip(const char *__restrict__ src, char *__restrict__ dst, const __grid_const
                                        smem_raw);
 }
 
-// Single domain with tensor-tile staging of the population rows (FP32):
-// `map` describes the source level (x, row, slot).
-template <class T, class ST, int SW, int DEPTH>
+// A single domain or a y-slab with tensor-tile staging of the population
+// rows (FP32): `map` describes the source level (x, row, slot).
+template <class T, class ST, int SW, int DEPTH, bool SLAB = false>
 __global__ void __launch_bounds__(strip_threads(SW), (StripSmem<T, ST, SW, DEPTH>::MINB))
 k_strip_tma(const char *__restrict__ src, char *__restrict__ dst, const __grid_constant__ KP<T> P,
             int seg_h, const __grid_constant__ CUtensorMap map) {
     extern __shared__ __align__(128) char smem_raw[];
     const int ys = P.ya + blockIdx.y * seg_h;
-    strip_body<T, ST, SW, DEPTH, false, true>(src, dst, P, blockIdx.x * SW, ys, min(ys + seg_h, P.yb),
-                                              smem_raw, &map);
+    strip_body<T, ST, SW, DEPTH, SLAB, true>(src, dst, P, blockIdx.x * SW, ys, min(ys + seg_h, P.yb),
+                                             smem_raw, &map);
 }
 
 // ---------------------------------------------------------------- batches
