@@ -393,7 +393,7 @@ def measure_lagged(lbm, p, phi, args, peak, mlups_sync, dist):
     return {"mlups": round(mlups, 2), "ms_per_step": round(total / args.steps, 5),
             "vs_synchronous": round(mlups / mlups_sync, 4), "bytes_per_cell": bpc,
             "hbm_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
-            "traffic": _traffic("lag_f32"), "kernel": "k_strip_lag<float>",
+            "traffic": _traffic("lag_f32"), "kernel": "k_strip_lag_tma<float> (interior strips' g and f rows by TMA tensor tiles)",
             "max_abs_diff_vs_synchronous": diff, "steps_for_diff": args.steps + args.warmup}
 
 

@@ -346,7 +346,7 @@ lbm_status lbm_bind_buffers(lbm_sim *s, void *state, size_t state_bytes, void *w
     s->d.err = reinterpret_cast<unsigned *>(s->work + s->L.out_off + 132);
     // tensor maps of the two levels for the tensor-tile staging
     s->d.tm_base[0] = s->d.tm_base[1] = nullptr;
-    if (s->ops->tma_box > 0 && !s->d.lag && s->ops->strip_ok(s->d))
+    if (s->ops->tma_box > 0 && s->ops->strip_ok(s->d))
         for (int i = 0; i < 2; ++i)
             if (encode_level_map(&s->d.tm[i], s->level(i), s->d, s->ops->tma_box))
                 s->d.tm_base[i] = s->level(i);

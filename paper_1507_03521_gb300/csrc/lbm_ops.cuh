@@ -166,23 +166,51 @@ struct OpsImpl {
         if constexpr (kDev) return cudaErrorNotSupported;
         else return lag_step_impl(d, src, dst, s);
     }
+    // tensor-tile staging of the lagged variant's g and f rows (FP32)
+    static constexpr bool kTmaLag = std::is_same<ST, PlainStore<float>>::value && LS::TMA_ROWS;
+    // strips x segments ~= the resident CTAs c allows, segments >= 16 rows
+    static void lag_grid(const Derived &d, const StripCfg &c, dim3 &grid, int &seg_h) {
+        const int strips = (d.nx + SW - 1) / SW;
+        long long nseg = (long long)c.per_sm * c.sms / strips;
+        if (nseg < 1) nseg = 1;
+        const long long max_seg = (d.ny + 15) / 16;
+        if (nseg > max_seg) nseg = max_seg;
+        seg_h = (int)((d.ny + nseg - 1) / nseg);
+        nseg = (d.ny + seg_h - 1) / seg_h;
+        grid = dim3((unsigned)strips, (unsigned)nseg);
+    }
     static cudaError_t lag_step_impl(const Derived &d, const void *src, void *dst, cudaStream_t s) {
+        if constexpr (kTmaLag) {
+            if (const CUtensorMap *m = d.map_for(src)) return lag_step_tma(d, src, dst, *m, s);
+        }
         static PerDevice<StripCfg> cfg;
         StripCfg c;
         cudaError_t e = cfg.get(c, [](int dev, StripCfg &v) {
             return strip_cfg(k_strip_lag<T, ST, SW, DEPTH>, (int)LS::bytes, dev, v);
         });
         if (e != cudaSuccess) return e;
-        const int strips = (d.nx + SW - 1) / SW;
-        long long nseg = (long long)c.per_sm * c.sms / strips;
-        if (nseg < 1) nseg = 1;
-        const long long max_seg = (d.ny + 15) / 16;
-        if (nseg > max_seg) nseg = max_seg;
-        const int seg_h = (int)((d.ny + nseg - 1) / nseg);
-        nseg = (d.ny + seg_h - 1) / seg_h;
-        k_strip_lag<T, ST, SW, DEPTH><<<dim3((unsigned)strips, (unsigned)nseg), NT, LS::bytes, s>>>(
+        dim3 grid;
+        int seg_h = 0;
+        lag_grid(d, c, grid, seg_h);
+        k_strip_lag<T, ST, SW, DEPTH><<<grid, NT, LS::bytes, s>>>(
             static_cast<const char *>(src), static_cast<char *>(dst), make_kp<T>(d),
             (long long)p_offset(d.NS), seg_h);
+        return cudaGetLastError();
+    }
+    static cudaError_t lag_step_tma(const Derived &d, const void *src, void *dst, const CUtensorMap &m,
+                                    cudaStream_t s) {
+        static PerDevice<StripCfg> cfg;
+        StripCfg c;
+        cudaError_t e = cfg.get(c, [](int dev, StripCfg &v) {
+            return strip_cfg(k_strip_lag_tma<T, ST, SW, DEPTH>, (int)LS::bytes_tma, dev, v);
+        });
+        if (e != cudaSuccess) return e;
+        dim3 grid;
+        int seg_h = 0;
+        lag_grid(d, c, grid, seg_h);
+        k_strip_lag_tma<T, ST, SW, DEPTH><<<grid, NT, LS::bytes_tma, s>>>(
+            static_cast<const char *>(src), static_cast<char *>(dst), make_kp<T>(d),
+            (long long)p_offset(d.NS), seg_h, m);
         return cudaGetLastError();
     }
 

@@ -47,6 +47,13 @@ struct LagSmem {
     static constexpr size_t pop_bytes = gb * NBG + fb * NBF + pb * NBP;
     static constexpr size_t bytes = pop_bytes + sizeof(T) * ((size_t)RPHI * WPHI + (size_t)RMU * WMU);
     static_assert(CHP <= strip_threads(SW), "one P chunk per thread");
+    // tensor-tile staging of the g and f rows (FP32), as in StripSmem: the
+    // rows issued in one iteration complete on one of DEPTH + 1 mbarriers
+    // after the rings; row buffers on 128-byte boundaries
+    static constexpr int NBAR = DEPTH + 1;
+    static constexpr size_t bar_off = (bytes + 7) / 8 * 8;
+    static constexpr size_t bytes_tma = bar_off + 8 * (size_t)NBAR;
+    static constexpr bool TMA_ROWS = gb % 128 == 0 && fb % 128 == 0;
 };
 
 // Ring slots (byte offsets into shared memory) of the rows live at
@@ -119,11 +126,14 @@ __device__ __forceinline__ void push_general(char *dst, const KP<T> &P, T fv[9],
 }
 
 // One work item: columns x0 .. x0+SW-1, rows ys .. ye-1.  `poff` is the
-// byte offset of the P slot within a level.
-template <class T, class ST, int SW, int DEPTH>
+// byte offset of the P slot within a level.  TMA: `map` is the source
+// level's 3-D tensor map; strips whose rows do not wrap in x take their g
+// and f rows from it (the P rows stay 16-byte chunk copies).
+template <class T, class ST, int SW, int DEPTH, bool TMA = false>
 __device__ __forceinline__ void strip_body_lag(const char *__restrict__ src, char *__restrict__ dst,
                                                const KP<T> &P, long long poff, const int x0,
-                                               const int ys, const int ye, char *smem_raw) {
+                                               const int ys, const int ye, char *smem_raw,
+                                               const CUtensorMap *map = nullptr) {
     using LS = LagSmem<T, ST, SW, DEPTH>;
     using SR = typename LS::SR;
     using C = typename LS::C;
@@ -140,6 +150,16 @@ __device__ __forceinline__ void strip_body_lag(const char *__restrict__ src, cha
     int pgo = -1;
     if (t < LS::CHP && t * LS::CEP < active + 2 * LS::CEP)
         pgo = wrap_any(x0 - LS::CEP + t * LS::CEP, nx);
+    const bool tma = TMA && x0 - HP >= 0 && x0 - HP + SR::LW <= nx;
+    unsigned bars = 0;
+    if constexpr (TMA) {
+        static_assert(LS::TMA_ROWS, "TMA rows need 128-byte aligned row buffers");
+        bars = smem_u32(smem_raw + LS::bar_off);
+        if (tma && t == 0) {
+            for (int k = 0; k < LS::NBAR; ++k) mbar_init(bars + 8 * k, 1);
+            mbar_init_fence();
+        }
+    }
     __syncthreads();
 
     LagRings<LS> R;
@@ -149,12 +169,30 @@ __device__ __forceinline__ void strip_body_lag(const char *__restrict__ src, cha
     const C *Psrc = reinterpret_cast<const C *>(src + poff);
     C *Pdst = reinterpret_cast<C *>(dst + poff);
 
+    // Barrier and phase parity of the rows issued for iteration it (the
+    // NBAR barriers in turn from yfirst on, each once every NBAR
+    // iterations).
+    auto ibar = [&](int it) { return bars + 8u * (unsigned)((it - yfirst) % LS::NBAR); };
+    auto ipar = [&](int it) { return (unsigned)((it - yfirst) / LS::NBAR) & 1u; };
     // Iteration y reads g row y+2, f row y and P row y+1 first; all are
-    // issued DEPTH iterations earlier, as one commit group.
+    // issued DEPTH iterations earlier, as one commit group (and, with
+    // tensor tiles, the g and f rows on one mbarrier).  Every iteration of
+    // the loop has its g row, so every barrier it waits on was armed.
     auto issue_for = [&](int it, int gslot, int fslot, int pslot) {
         const int gr = it + 2, fr = it, pr = it + 1;
-        if (gr <= ye + 1) SR::issue_g(desc, at(gslot), src, src_row(gr, ny, wall) * nx);
-        if (fr >= ys && fr < ye) SR::issue_f(desc, at(fslot), src, src_row(fr, ny, wall) * nx);
+        const bool g_in = gr <= ye + 1, f_in = fr >= ys && fr < ye;
+        if (tma) {
+            if (t == 0 && (g_in || f_in)) {
+                constexpr unsigned row_bytes = (unsigned)(9 * SR::LW * sizeof(T));
+                const unsigned bar = ibar(it);
+                mbar_expect_tx(bar, (g_in ? row_bytes : 0u) + (f_in ? row_bytes : 0u) + P.tx_extra);
+                if (g_in) tma_load_3d(smem_u32(at(gslot)), map, bar, x0 - HP, src_row(gr, ny, wall), 9);
+                if (f_in) tma_load_3d(smem_u32(at(fslot)), map, bar, x0 - HP, src_row(fr, ny, wall), 0);
+            }
+        } else {
+            if (g_in) SR::issue_g(desc, at(gslot), src, src_row(gr, ny, wall) * nx);
+            if (f_in) SR::issue_f(desc, at(fslot), src, src_row(fr, ny, wall) * nx);
+        }
         if (pr >= ys - 1 && pr <= ye && pgo >= 0)
             cp_async16(atC(pslot) + t * LS::CEP, Psrc + (src_row(pr, ny, wall) * nx + pgo));
         cp_async_commit();
@@ -166,8 +204,22 @@ __device__ __forceinline__ void strip_body_lag(const char *__restrict__ src, cha
     const T c6 = T(0.5 / 3.0);
 
     for (int y = yfirst; y < ye; ++y) {
-        cp_async_wait<DEPTH - 1>();
-        __syncthreads();
+        cp_async_wait<DEPTH - 1>();  // this thread's P chunk of row y+1
+        if (tma) {
+            // g row y+2 and f row y have landed (bounded wait); the CTA
+            // barrier also publishes every thread's P chunk
+            if (__syncthreads_or(!mbar_wait(ibar(y), ipar(y)))) {
+                if (t == 0 && P.err) atomicOr(P.err, 1u);
+                // the loads of iterations y+1 .. y+DEPTH-1 are still in
+                // flight into this CTA's shared memory: wait (bounded)
+                for (int d = 1; d < DEPTH; ++d)
+                    if (y + d < ye) mbar_wait(ibar(y + d), ipar(y + d));
+                cp_async_wait<0>();
+                return;
+            }
+        } else {
+            __syncthreads();
+        }
         issue_for(y + DEPTH, R.g[LS::NBG - 1], R.f[LS::NBF - 1], R.p[LS::NBP - 1]);
 
         // 1. phi at row y+2, columns -2 .. SW+1
@@ -279,6 +331,18 @@ k_strip_lag(const char *__restrict__ src, char *__restrict__ dst, const __grid_c
     const int ys = blockIdx.y * seg_h;
     strip_body_lag<T, ST, SW, DEPTH>(src, dst, P, poff, blockIdx.x * SW, ys,
                                      min(ys + seg_h, P.ny), smem_raw);
+}
+
+// The same with tensor-tile staging of the g and f rows (FP32): `map`
+// describes the source level (x, row, slot).
+template <class T, class ST, int SW, int DEPTH>
+__global__ void __launch_bounds__(strip_threads(SW))
+k_strip_lag_tma(const char *__restrict__ src, char *__restrict__ dst, const __grid_constant__ KP<T> P,
+                long long poff, int seg_h, const __grid_constant__ CUtensorMap map) {
+    extern __shared__ __align__(128) char smem_raw[];
+    const int ys = blockIdx.y * seg_h;
+    strip_body_lag<T, ST, SW, DEPTH, true>(src, dst, P, poff, blockIdx.x * SW, ys,
+                                           min(ys + seg_h, P.ny), smem_raw, &map);
 }
 
 }  // namespace lbm

@@ -1,4 +1,5 @@
-"""The lagged-grad-p variant on the GPU (k_strip_lag) against the oracle's
+"""The lagged-grad-p variant on the GPU (k_strip_lag, and k_strip_lag_tma for
+FP32 strips whose rows come as tensor tiles) against the oracle's
 lagged variant, element by element: FP64 within the FP64 bar, FP32 within
 1e-5 on phi and u; resume from a saved state (which carries the stored
 pressure) is bit-identical; the variant is refused where it is not built."""
@@ -56,7 +57,9 @@ def test_lagged_f64_matches_oracle(L, c):
     check64(got, ref, oracle_spread(p, phi, ux, uy, steps, ref), f"lagged {c['shape']}")
 
 
-@pytest.mark.parametrize("c", CASES[:3], ids=lambda c: "x".join(map(str, c["shape"])))
+# 264 and 392 columns: the middle strips take their g and f rows as
+# tensor tiles (k_strip_lag_tma), periodic and walled
+@pytest.mark.parametrize("c", CASES[:4], ids=lambda c: "x".join(map(str, c["shape"])))
 def test_lagged_f32_matches_oracle(L, c):
     p, phi, ux, uy = _case(c)
     steps = 40
