@@ -231,22 +231,40 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // the level use the map).  False when the map cannot be made; the strip
 // kernel then copies by chunks.
 namespace lbm {
-bool encode_level_map(CUtensorMap *m, const void *lvl, const Derived &d, int box) {
+// One 3-D map (x, row, slot) of `nslots` slots of `elem`-byte elements,
+// slot s at byte offset s * slot_stride from base; boxes box x 1 x bslots.
+static bool encode_map(CUtensorMap *m, CUtensorMapDataType type, const void *base, int nx, int rows,
+                       int nslots, int elem, size_t slot_stride, int box, int bslots) {
     const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (!enc || box <= 0 || box > 256) return false;
+    if (!enc || box <= 0 || box > 256 || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)rows, (cuuint64_t)nslots};
+    cuuint64_t strides[2] = {(cuuint64_t)nx * elem, (cuuint64_t)slot_stride};
+    cuuint32_t boxd[3] = {(cuuint32_t)box, 1, (cuuint32_t)bslots};
+    cuuint32_t estr[3] = {1, 1, 1};
+    if (((strides[0] | strides[1]) & 15) || ((size_t)box * elem) % 16) return false;
+    return enc(m, type, 3, const_cast<void *>(base), dims, strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool encode_level_maps(CUtensorMap *m, const void *lvl, const Derived &d, int kind, int box) {
     // rows a level holds: the domain's, or a y-slab's own rows and ghosts
     const int rows = d.slab ? d.rows : d.ny;
-    cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)rows, 18};
-    cuuint64_t strides[2] = {(cuuint64_t)d.nx * 4, (cuuint64_t)d.NS * 4};
-    cuuint32_t boxd[3] = {(cuuint32_t)box, 1, 9};
-    cuuint32_t estr[3] = {1, 1, 1};
-    if ((strides[0] | strides[1]) & 15) return false;
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(lvl), dims, strides, boxd, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    const char *b = static_cast<const char *>(lvl);
+    if (kind == kTmaPlain32)  // f_0..f_8, g_0..g_8 as FP32 slots NS apart
+        return encode_map(&m[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, b, d.nx, rows, 18, 4,
+                          (size_t)d.NS * 4, box, 9);
+    if (kind == kTmaHalf)  // g_0 as NS floats, then 17 half slots NS apart
+        return encode_map(&m[0], CU_TENSOR_MAP_DATA_TYPE_UINT16, b + (size_t)d.NS * 4, d.nx, rows, 17, 2,
+                          (size_t)d.NS * 2, box, 9) &&
+               encode_map(&m[1], CU_TENSOR_MAP_DATA_TYPE_UINT16, b + (size_t)d.NS * 4, d.nx, rows, 17, 2,
+                          (size_t)d.NS * 2, box, 8) &&
+               encode_map(&m[2], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, b, d.nx, rows, 1, 4, (size_t)d.NS * 4,
+                          box, 1);
+    return false;
 }
 }  // namespace lbm
-using lbm::encode_level_map;
+using lbm::encode_level_maps;
 
 // The kernels' error word: bit 0, a bounded wait for a tile load ran out.
 static lbm_status error_word(lbm_sim *s) {
@@ -346,9 +364,9 @@ lbm_status lbm_bind_buffers(lbm_sim *s, void *state, size_t state_bytes, void *w
     s->d.err = reinterpret_cast<unsigned *>(s->work + s->L.out_off + 132);
     // tensor maps of the two levels for the tensor-tile staging
     s->d.tm_base[0] = s->d.tm_base[1] = nullptr;
-    if (s->ops->tma_box > 0 && s->ops->strip_ok(s->d))
+    if (s->ops->tma_kind > 0 && s->ops->strip_ok(s->d))
         for (int i = 0; i < 2; ++i)
-            if (encode_level_map(&s->d.tm[i], s->level(i), s->d, s->ops->tma_box))
+            if (encode_level_maps(s->d.tm[i], s->level(i), s->d, s->ops->tma_kind, s->ops->tma_box))
                 s->d.tm_base[i] = s->level(i);
     return LBM_OK;
 }
@@ -595,7 +613,8 @@ static cudaError_t adj_recompute_issue(lbm_sim *s, int64_t n, char *states, size
     for (int64_t k = 1; k < n; ++k) {
         char *src = states + (k - 1) * lb;
         dk.tm_base[0] = dk.tm_base[1] = nullptr;
-        if (s->d.tm_base[0] && encode_level_map(&dk.tm[0], src, dk, o->tma_box)) dk.tm_base[0] = src;
+        if (s->d.tm_base[0] && encode_level_maps(dk.tm[0], src, dk, o->tma_kind, o->tma_box))
+            dk.tm_base[0] = src;
         cudaError_t e = o->step(dk, src, states + k * lb, st);
         if (e != cudaSuccess) return e;
     }

@@ -58,6 +58,10 @@ struct PerDevice {
     }
 };
 
+// Tensor maps per level at most (16-bit storage: half slots in boxes of 9
+// and of 8, and the g_0 floats).
+constexpr int kMaxLevelMaps = 3;
+
 // Host-side derived parameters of one domain (FP64).
 struct Derived {
     int nx, ny, wall;
@@ -77,14 +81,14 @@ struct Derived {
     // test hook (lbm_test_unfinished_tiles): bytes each tile load announces
     // beyond what it brings, so that its wait runs out; 0 in normal use
     unsigned tx_extra = 0;
-    // 3-D tensor maps (x, row, slot) of the handle's two levels, for the
-    // tensor-tile staging of FP32 single domains; tm_base[i] is the level
-    // map i describes (null: none)
+    // 3-D tensor maps (x, row, slot) of the two levels, for the tensor-tile
+    // staging of population rows (FP32: one map per level; 16-bit storage:
+    // three); tm_base[i] is the level maps tm[i] describe (null: none)
     const void *tm_base[2] = {nullptr, nullptr};
-    CUtensorMap tm[2];
+    CUtensorMap tm[2][kMaxLevelMaps];
     const CUtensorMap *map_for(const void *lvl) const {
         for (int i = 0; i < 2; ++i)
-            if (tm_base[i] && tm_base[i] == lvl) return &tm[i];
+            if (tm_base[i] && tm_base[i] == lvl) return tm[i];
         return nullptr;
     }
     double phiA, phiB, phibar, rhoB, drho;
@@ -92,10 +96,12 @@ struct Derived {
     double grav, rhoref, tau_f, tau_g, uwb, uwt;
 };
 
-// The 3-D tensor map (x, row, slot) of one FP32 level of d (a whole domain
-// or a y-slab), with boxes of `box` columns x 1 row x 9 slots; false where
-// the driver entry point is missing or the level cannot be described.
-bool encode_level_map(CUtensorMap *m, const void *lvl, const Derived &d, int box);
+// The 3-D tensor maps (x, row, slot) of one level of d (a whole domain or a
+// y-slab) for the tensor-tile row loads of storage kind `kind` (Ops::
+// tma_kind), with boxes `box` columns wide, into m[0 .. kMaxLevelMaps);
+// false where the driver entry point is missing or the level cannot be
+// described.
+bool encode_level_maps(CUtensorMap *m, const void *lvl, const Derived &d, int kind, int box);
 
 // Extra constants of the adjoint: derivatives of the model constants with
 // respect to M and sigma.
@@ -161,10 +167,14 @@ struct Ops {
                                      unsigned long long *tickets, int parity, int grid, cudaStream_t s);
     // NVTX range name of one step launch ("step <name>")
     const char *step_range = "step";
-    // width (x extent) of the tensor-map box of the tensor-tile staging, 0
-    // where the form does not use it
+    // tensor-tile staging of population rows: the maps' box width (x
+    // extent) and the level layout they describe (kTmaPlain32: 18 FP32
+    // slots; kTmaHalf: g_0 floats and 17 half slots); 0 where the form does
+    // not use it
     int tma_box = 0;
+    int tma_kind = 0;
 };
+constexpr int kTmaPlain32 = 1, kTmaHalf = 2;
 
 const Ops *ops_f64();
 const Ops *ops_f32();

@@ -123,14 +123,18 @@ struct OpsImpl {
         if constexpr (kDev && SLAB) return cudaErrorNotSupported;
         else return strip_step_impl<SLAB>(d, src, dst, s);
     }
-    // tensor-tile staging: FP32 single domains and y-slabs whose rows are
-    // 128-byte aligned row buffers (the 120-column strips)
-    static constexpr bool kTma = std::is_same<ST, PlainStore<float>>::value && SM::TMA_ROWS;
+    // tensor-tile staging: single domains and y-slabs of FP32 and of raw
+    // 16-bit storage on the 120-column strips (128-byte aligned row buffers)
+    static constexpr bool kTmaPlain = std::is_same<ST, PlainStore<float>>::value;
+    static constexpr bool kTmaHalfSt = std::is_same<ST, Store16<__half>>::value ||
+                                       std::is_same<ST, Store16<__nv_bfloat16>>::value;
+    static constexpr bool kTma = (kTmaPlain || kTmaHalfSt) && SM::TMA_ROWS && SW == 120;
+    static constexpr int kTmaKind = kTma ? (kTmaPlain ? kTmaPlain32 : kTmaHalf) : 0;
 
     template <bool SLAB>
     static cudaError_t strip_step_impl(const Derived &d, const void *src, void *dst, cudaStream_t s) {
         if constexpr (kTma) {
-            if (const CUtensorMap *m = d.map_for(src)) return strip_step_tma<SLAB>(d, src, dst, *m, s);
+            if (const CUtensorMap *m = d.map_for(src)) return strip_step_tma<SLAB>(d, src, dst, m, s);
         }
         dim3 grid;
         int seg_h = 0;
@@ -143,7 +147,9 @@ struct OpsImpl {
 
     template <bool SLAB>
     static cudaError_t strip_step_tma(const Derived &d, const void *src, void *dst,
-                                      const CUtensorMap &m, cudaStream_t s) {
+                                      const CUtensorMap *m, cudaStream_t s) {
+        TmaMaps<StripRow<ST, SW>::NMAP> mm;
+        for (int i = 0; i < StripRow<ST, SW>::NMAP; ++i) mm.m[i] = m[i];
         static PerDevice<StripCfg> cfg;
         StripCfg c;
         cudaError_t e = cfg.get(c, [](int dev, StripCfg &v) {
@@ -154,7 +160,7 @@ struct OpsImpl {
         int seg_h = 0;
         one_wave(d, c, grid, seg_h);
         k_strip_tma<T, ST, SW, DEPTH, SLAB><<<grid, NT, SM::bytes_tma, s>>>(
-            static_cast<const char *>(src), static_cast<char *>(dst), make_kp<T>(d), seg_h, m);
+            static_cast<const char *>(src), static_cast<char *>(dst), make_kp<T>(d), seg_h, mm);
         return cudaGetLastError();
     }
 
@@ -434,6 +440,7 @@ struct OpsImpl {
         static const std::string range = std::string("step ") + name;
         o.step_range = range.c_str();
         o.tma_box = kTma ? SM::LW : 0;
+        o.tma_kind = kTmaKind;
         if constexpr (!std::is_same<BN, void>::value) {
             o.narrow_width = BN::kSW;
             o.batch_slots_narrow = &BN::batch_slots;

@@ -251,8 +251,8 @@ lbm_status lbm_slabs_bind_buffers(lbm_slabs *s, void *state, size_t state_bytes,
         Derived &d = s->P.ds[i];
         for (int lv = 0; lv < 2; ++lv) {
             d.tm_base[lv] = nullptr;
-            if (s->ops->tma_box > 0 &&
-                lbm::encode_level_map(&d.tm[lv], s->level(i, lv), d, s->ops->tma_box))
+            if (s->ops->tma_kind > 0 &&
+                lbm::encode_level_maps(d.tm[lv], s->level(i, lv), d, s->ops->tma_kind, s->ops->tma_box))
                 d.tm_base[lv] = s->level(i, lv);
         }
     }

@@ -197,6 +197,18 @@ struct StripRow<PlainStore<T>, SW> {
 #pragma unroll
         for (int i = 0; i < 9; ++i) g[i] = s[i * LW + c];
     }
+    // Tensor-tile rows (one map per level: x, row, 18 slots): the g row is
+    // the box at slot 9, the f row the box at slot 0.
+    static constexpr int NMAP = 1;
+    static constexpr unsigned TMA_GB = (unsigned)(9 * LW * sizeof(T)), TMA_FB = TMA_GB;
+    __device__ __forceinline__ static void tma_g(unsigned dst, const CUtensorMap *m, unsigned bar,
+                                                 int x, int row) {
+        tma_load_3d(dst, m, bar, x, row, 9);
+    }
+    __device__ __forceinline__ static void tma_f(unsigned dst, const CUtensorMap *m, unsigned bar,
+                                                 int x, int row) {
+        tma_load_3d(dst, m, bar, x, row, 0);
+    }
     // Interior push: slot i of cell kb + cy_i nx + cx_i, 32-bit offsets.
     __device__ __forceinline__ static void store_fast(char *lvl, int NS, int nx, int kb,
                                                       const C fv[9], const C gv[9], C phi) {
@@ -220,11 +232,28 @@ struct StripRow<Store16<H>, SW> {
     static constexpr int TG = C0 + 8 * CH;          // g row: g_0 floats, half slots 9..16
     static constexpr int NT = strip_threads(SW);
     static constexpr int NF = (TF + NT - 1) / NT, NG = (TG + NT - 1) / NT;
+    // a g row holds the g_0 floats, padded to a 128-byte multiple so that
+    // its half slots start on a tensor-tile boundary, then half slots 9..16
+    static constexpr int G0B = (LW * 4 + 127) / 128 * 128;
     static constexpr size_t fbytes = (size_t)9 * LW * 2;
-    static constexpr size_t gbytes = (size_t)LW * 4 + (size_t)8 * LW * 2;
+    static constexpr size_t gbytes = (size_t)G0B + (size_t)8 * LW * 2;
     // offsets count halves from the level base: half slot s starts at half
     // index (2 + s) NS, after the NS floats of g_0
     static bool idx32_ok(long long NS) { return 19 * NS < (1LL << 31); }
+    // Tensor-tile rows, three maps per level: [0] the 17 half slots with
+    // boxes of 9 slots (the f row: slots 0..8), [1] the same with boxes of 8
+    // (the g row's slots 9..16), [2] the g_0 floats (one slot).
+    static constexpr int NMAP = 3;
+    static constexpr unsigned TMA_GB = (unsigned)(LW * 4 + 8 * LW * 2), TMA_FB = (unsigned)(9 * LW * 2);
+    __device__ __forceinline__ static void tma_g(unsigned dst, const CUtensorMap *m, unsigned bar,
+                                                 int x, int row) {
+        tma_load_3d(dst, m + 2, bar, x, row, 0);
+        tma_load_3d(dst + G0B, m + 1, bar, x, row, 9);
+    }
+    __device__ __forceinline__ static void tma_f(unsigned dst, const CUtensorMap *m, unsigned bar,
+                                                 int x, int row) {
+        tma_load_3d(dst, m, bar, x, row, 0);
+    }
 
     struct Desc {
         int foff[NF], fso[NF];      // f chunks: global half offset, smem half offset
@@ -258,7 +287,7 @@ struct StripRow<Store16<H>, SW> {
                 const int jj = j - C0;
                 const int sl = jj / CH, c = jj - sl * CH;
                 d.goff[k] = (2 + 9 + sl) * ns + wrap_any(x_start + c * 8, nx);
-                d.gso[k] = LW * 4 + (sl * LW + c * 8) * 2;  // bytes
+                d.gso[k] = G0B + (sl * LW + c * 8) * 2;  // bytes
             } else {
                 d.goff[k] = -1;
                 d.gso[k] = 0;
@@ -292,7 +321,7 @@ struct StripRow<Store16<H>, SW> {
     }
     __device__ __forceinline__ static void read_g(const char *gbuf, int c, C g[9]) {
         const float *s0 = reinterpret_cast<const float *>(gbuf);
-        const unsigned short *sh = reinterpret_cast<const unsigned short *>(gbuf + (size_t)LW * 4);
+        const unsigned short *sh = reinterpret_cast<const unsigned short *>(gbuf + G0B);
         g[0] = s0[c];
 #pragma unroll
         for (int i = 1; i < 9; ++i) g[i] = E::dec(sh[(i - 1) * LW + c]);
@@ -464,8 +493,9 @@ struct StripSmem {
     static constexpr bool DEV = IsDev<ST>::value;
     static constexpr int RPHI = 4, RMU = DEV ? 4 : 3, RP = 3, MU0 = RMU - 3;
     static constexpr int WPHI = SW + 6, WMU = SW + 4, WQ = SW + 2;
-    static constexpr size_t gb = (SR::gbytes + 15) / 16 * 16;
-    static constexpr size_t fb = (SR::fbytes + 15) / 16 * 16;
+    // row buffers on 128-byte boundaries (tensor-tile destinations)
+    static constexpr size_t gb = (SR::gbytes + 127) / 128 * 128;
+    static constexpr size_t fb = (SR::fbytes + 127) / 128 * 128;
     static constexpr size_t pop_bytes = gb * NBG + fb * NBF;
     static constexpr size_t fld_elems =
         (size_t)RPHI * WPHI + (size_t)RMU * WMU + (size_t)RP * WQ;
@@ -736,20 +766,21 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     const int lvl_rows = SLAB ? P.rows : ny;  // rows a level holds
     auto issue_for = [&](int it, int gslot, int fslot) {
         const int gr = it + 3, fr = it + 1;
-        if (tma) {
-            // one arrival announcing both rows' bytes, then the two loads
-            const bool g_in = gr <= ye + 2, f_in = fr >= ys - 1 && fr <= ye;
-            if (t == 0 && (g_in || f_in)) {
-                const int bg = buf_row<SLAB>(P, gr), bf = buf_row<SLAB>(P, fr);
-                const bool gok = g_in && LBM_IDX_OK(P, bg >= 0 && bg < lvl_rows, 1);
-                const bool fok = f_in && LBM_IDX_OK(P, bf >= 0 && bf < lvl_rows, 1);
-                constexpr unsigned row_bytes = (unsigned)(9 * SR::LW * sizeof(T));
-                const unsigned bar = ibar(it);
-                mbar_expect_tx(bar, (gok ? row_bytes : 0u) + (fok ? row_bytes : 0u) + P.tx_extra);
-                if (gok) tma_load_3d(smem_u32(at(gslot)), map, bar, x0 - HP, bg, 9);
-                if (fok) tma_load_3d(smem_u32(at(fslot)), map, bar, x0 - HP, bf, 0);
+        if constexpr (TMA) {
+            if (tma) {
+                // one arrival announcing both rows' bytes, then the loads
+                const bool g_in = gr <= ye + 2, f_in = fr >= ys - 1 && fr <= ye;
+                if (t == 0 && (g_in || f_in)) {
+                    const int bg = buf_row<SLAB>(P, gr), bf = buf_row<SLAB>(P, fr);
+                    const bool gok = g_in && LBM_IDX_OK(P, bg >= 0 && bg < lvl_rows, 1);
+                    const bool fok = f_in && LBM_IDX_OK(P, bf >= 0 && bf < lvl_rows, 1);
+                    const unsigned bar = ibar(it);
+                    mbar_expect_tx(bar, (gok ? SR::TMA_GB : 0u) + (fok ? SR::TMA_FB : 0u) + P.tx_extra);
+                    if (gok) SR::tma_g(smem_u32(at(gslot)), map, bar, x0 - HP, bg);
+                    if (fok) SR::tma_f(smem_u32(at(fslot)), map, bar, x0 - HP, bf);
+                }
+                return;
             }
-            return;
         }
         if (gr <= ye + 2) {
             const int b = buf_row<SLAB>(P, gr);
@@ -1036,16 +1067,22 @@ k_strip(const char *__restrict__ src, char *__restrict__ dst, const __grid_const
                                        smem_raw);
 }
 
+// The tensor maps of one level that a storage type's row loads use.
+template <int N>
+struct TmaMaps {
+    CUtensorMap m[N];
+};
+
 // A single domain or a y-slab with tensor-tile staging of the population
-// rows (FP32): `map` describes the source level (x, row, slot).
+// rows (FP32 and 16-bit storage): `maps` describe the source level.
 template <class T, class ST, int SW, int DEPTH, bool SLAB = false>
 __global__ void __launch_bounds__(strip_threads(SW), (StripSmem<T, ST, SW, DEPTH>::MINB))
 k_strip_tma(const char *__restrict__ src, char *__restrict__ dst, const __grid_constant__ KP<T> P,
-            int seg_h, const __grid_constant__ CUtensorMap map) {
+            int seg_h, const __grid_constant__ TmaMaps<StripRow<ST, SW>::NMAP> maps) {
     extern __shared__ __align__(128) char smem_raw[];
     const int ys = P.ya + blockIdx.y * seg_h;
     strip_body<T, ST, SW, DEPTH, SLAB, true>(src, dst, P, blockIdx.x * SW, ys, min(ys + seg_h, P.yb),
-                                             smem_raw, &map);
+                                             smem_raw, maps.m);
 }
 
 // ---------------------------------------------------------------- batches

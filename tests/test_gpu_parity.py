@@ -271,6 +271,19 @@ def test_16bit_storage_error_and_conservation(lbm, dtype, tol):
     assert abs(t1 - t0) <= 2e-5 * np.abs(phi).sum()
 
 
+@pytest.mark.parametrize("dtype,tol", [("f16s", 2e-3), ("bf16s", 3e-2)])
+def test_16bit_tensor_tile_strips_match_oracle(lbm, dtype, tol):
+    """Raw 16-bit storage on a 368-column walled grid, whose two middle
+    strips load their rows as tensor tiles: phi and u within the 16-bit
+    bounds of the FP64 oracle, sum phi conserved to FP32 rounding."""
+    p, phi, ux, uy = W.small_case(368, 45, seed=22, walls=True, gravity=1e-5, u_wall=0.01)
+    g, gm = _run_gpu(lbm, p, phi, ux, uy, 60, dtype)
+    o, om, _ = _run_orc(p, phi, ux, uy, 60)
+    assert np.abs(g["phi"] - o["phi"]).max() <= tol
+    assert max(np.abs(g["ux"] - o["ux"]).max(), np.abs(g["uy"] - o["uy"]).max()) <= tol * 0.1
+    assert abs(gm[1] - om[1]) <= 2e-5 * np.abs(phi).sum()
+
+
 def test_errors_surface_through_the_abi(lbm):
     p, phi = W.droplet64()
     s = lbm.Sim(p, "f32")
@@ -289,26 +302,29 @@ def test_errors_surface_through_the_abi(lbm):
     assert e.value.status == -3
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f16s", "bf16s"])
 @pytest.mark.parametrize("walls", [False, True])
-def test_tensor_tile_rows_equal_chunk_copies(lbm, walls):
-    """FP32 single domains stage the rows of strips that lie inside the
-    level by TMA tensor tiles; the batched form copies every row by 16-byte
-    chunks.  Same rows in shared memory and the same per-cell arithmetic,
-    so the two agree to FP32 rounding (different kernels may contract
-    multiply-adds differently; helpers.same_result)."""
+def test_tensor_tile_rows_equal_chunk_copies(lbm, walls, dtype):
+    """Single domains in FP32 and raw 16-bit storage stage the rows of
+    strips that lie inside the level by TMA tensor tiles (16-bit: the g_0
+    floats and the half slots from three maps); the batched form copies
+    every row by 16-byte chunks.  Same rows in shared memory and the same
+    per-cell arithmetic, so the two agree (helpers.same_result: FP32 to
+    rounding, since different kernels may contract multiply-adds
+    differently)."""
     p, phi, ux, uy = W.small_case(368, 61, seed=21, walls=walls, gravity=1e-5 if walls else 0.0,
                                   u_wall=0.01 if walls else 0.0)
-    s = lbm.Sim(p, "f32")
+    s = lbm.Sim(p, dtype)
     s.init_phi(phi)
     s.step(9)
     a = {k: v.cpu().numpy() for k, v in s.fields(("phi", "ux", "uy", "p")).items()}
     sm = s.mass()
     s.close()
-    b = lbm.Batch([p], "f32")
+    b = lbm.Batch([p], dtype)
     b.init_phi([phi])
     b.step(9)
     g = b.fields()[0]
     for k in a:
-        same_result(a[k], g[k].cpu().numpy(), "f32", k)
+        same_result(a[k], g[k].cpu().numpy(), dtype, k)
     assert abs(b.mass()[0][0] - sm[0]) <= 1e-9 * abs(sm[0])
     b.close()
