@@ -409,15 +409,17 @@ __device__ __forceinline__ void adj_theta_partials(double dM, double dS, double 
 
 // The mu and phi adjoints of a reverse step, and the fold of its (M, sigma)
 // partial sums, in one launch.  A CTA of 256 threads takes
-// 32 x 8 tiles in turn: it computes mu_bar on the tile and a ring of one
+// 64 x 8 tiles in turn: it computes mu_bar on the tile and a ring of one
 // cell into shared memory (the ring cells are recomputed by each
 // neighbouring tile and only read here), then the phi adjoint of the tile
 // from it.  Its inputs are final before the launch; its global writes are
 // the tile cells' lambda_t g slots and the CTA's (M, sigma) partial sums.
 // The last CTA to finish (a ticket counter; the counter is left at zero)
 // folds the partial sums into the running totals, in the same fixed order
-// as k_adj_accumulate.
-constexpr int kMpTX = 32, kMpTY = 8;
+// as k_adj_accumulate.  64-column tiles, two cells per thread: a 512^2
+// grid has 512 tiles, all resident at once (with 32-column tiles its 1024
+// tiles took two rounds of the 608 CTAs the partial sums allow).
+constexpr int kMpTX = 64, kMpTY = 8;
 
 template <class T>
 __global__ void __launch_bounds__(256) k_adj_muphi(T *__restrict__ lam, const AdjP<T> P, AdjW<T> W,
@@ -430,7 +432,7 @@ __global__ void __launch_bounds__(256) k_adj_muphi(T *__restrict__ lam, const Ad
     const KP<T> &K = P.k;
     const long long NS = K.NS;
     const int nx = B.nx, ny = B.ny;
-    const int tid = threadIdx.x, lx = tid % kMpTX, ly = tid / kMpTX;  // 1-D block of 256
+    const int tid = threadIdx.x;  // 1-D block of 256
     const int tilesx = (nx + kMpTX - 1) / kMpTX, tilesy = (ny + kMpTY - 1) / kMpTY;
     const long long ntiles = (long long)tilesx * tilesy;
     const T *gmx = W[B_GMUX], *gmy = W[B_GMUY], *bl = W[B_LMU];
@@ -459,8 +461,10 @@ __global__ void __launch_bounds__(256) k_adj_muphi(T *__restrict__ lam, const Ad
         }
         __syncthreads();
         // phi adjoint of the tile: grad phi and lap phi transposed, phi = sum g
-        const int x = tx0 + lx, y = ty0 + ly;
-        if (x < nx && y < ny) {
+        for (int j = tid; j < kMpTX * kMpTY; j += 256) {
+            const int lx = j % kMpTX, ly = j / kMpTX;
+            const int x = tx0 + lx, y = ty0 + ly;
+            if (x >= nx || y >= ny) continue;
             const long long k = (long long)y * nx + x;
             const int sx0 = lx + 1, sy0 = ly + 1;
             const T ph = W[A_PHI][k];
