@@ -338,7 +338,7 @@ def test_adjoint_full_workload_f32_close_to_f64(L):
         sg = torch.tensor(p["sigma"], dtype=torch.float64, requires_grad=True)
         loss = rollout_loss(ph, M, sg, p, steps, target, K=K, dtype=dt)
         loss.backward()
-        out[dt] = (float(loss), ph.grad.numpy().copy(), M.grad.item(), sg.grad.item())
+        out[dt] = (float(loss.detach()), ph.grad.numpy().copy(), M.grad.item(), sg.grad.item())
     l64, g64, m64, s64 = out["f64"]
     l32, g32, m32, s32 = out["f32"]
     eg = float(np.abs(g32 - g64).max() / np.abs(g64).max())
