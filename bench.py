@@ -432,7 +432,7 @@ def measure_3d(lbm, W, args, peak, dist):
             "finite": bool(np.isfinite(m0[0]))}
 
 
-def measure_adjoint(W):
+def measure_adjoint(W, peak):
     """Adjoint workload: droplet in shear, 512 x 512, R = 64, walls at
     +-0.01, rho ratio 10, FP32, 4000 steps, checkpoints every 200 steps;
     loss = sum (phi_T - phi_target)^2 with phi_target from a run at
@@ -465,6 +465,13 @@ def measure_adjoint(W):
             "dL_dphi0_norm": float(ph.grad.norm()),
             "forward_s": round(t1 - t0, 4), "backward_s": round(t2 - t1, 4),
             "backward_mlups": round(cells * steps / (t2 - t1) / 1e6, 2),
+            # 216 B per reverse cell-update: lambda_{t+1} read and lambda_t
+            # written (144 B) and the recomputed state read once (72 B); the
+            # 512^2 working set sits in L2, so latency, not HBM, bounds it
+            "bytes_per_cell": 216,
+            "hbm_gbs": round(216 * cells * steps / (t2 - t1) / 1e9, 1),
+            "frac": round(216 * cells * steps / (t2 - t1) / 1e9 / peak, 4),
+            "bound": "latency (L2-resident working set)",
             "note": "wall-clock incl. host loop; backward = recompute + adjoint steps"}
 
 
@@ -617,7 +624,7 @@ def main():
     if not args.no_3d:
         line["d3q19"] = measure_3d(lbm, W, args, peak, dist)
     if not args.no_adjoint:
-        line["adjoint"] = measure_adjoint(W)
+        line["adjoint"] = measure_adjoint(W, peak)
 
     # End to end through the C ABI with host buffers: phi0 in, K steps,
     # phi/u/p out and the mass diagnostic, all inside the timed region.
