@@ -74,9 +74,12 @@ def _kernel_hash(sources=STEP_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
-def _traffic(dtype: str, sources=STEP_SOURCES):
+def _traffic(dtype: str, sources=STEP_SOURCES, full_size=True):
     """DRAM bytes per launch of the step kernel from a committed ncu
-    summary, if it was taken on the current kernel sources."""
+    summary, if it was taken on the current kernel sources and the run is
+    on the workload it was taken on (full_size)."""
+    if not full_size:
+        return None
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -293,7 +296,8 @@ def measure_batch(lbm, W, args, peak, dist):
     the 128-column strip kernel per step over every (domain, strip,
     segment) item, replayed from a CUDA graph, segment height autotuned."""
     import torch
-    doms = W.batch_domains(1024, seed=1507036)
+    nd = args.batch_domains
+    doms = W.batch_domains(nd, seed=1507036)
     b = lbm.Batch([p for p, _ in doms], "f32", graph=True)
     phis = [phi for _, phi in doms]
     b.init_phi(phis)
@@ -316,13 +320,13 @@ def measure_batch(lbm, W, args, peak, dist):
     gbs = BYTES_PER_CELL["f32"] * cells / (ms / args.steps * 1e-3) / 1e9
     wide, narrow = b.work_items()
     b.close()
-    return {"workload": "batch-1024-domains-64to512", "domains": 1024, "cells": cells,
+    return {"workload": f"batch-{nd}-domains-64to512", "domains": nd, "cells": cells,
             "mlups": round(cells * args.steps * world / (ms * 1e-3) / 1e6, 2),
             "ms_per_step": round(ms / args.steps, 5), "hbm_gbs": round(gbs, 1),
             "frac": round(gbs / peak, 4), "seg_h": seg, "graph": True,
             "launches_per_step": 1, "items_per_step": [wide, narrow],
             "kernel": "k_strip_batch<float, 128 columns> (one launch per step over all items)",
-            "traffic": _traffic("batch_f32"), "bytes_alg": BYTES_PER_CELL["f32"] * cells}
+            "traffic": _traffic("batch_f32") if nd == 1024 else None, "bytes_alg": BYTES_PER_CELL["f32"] * cells}
 
 
 def measure_slabs(lbm, p, phi, args, mlups_single, dist, n_slabs=4):
@@ -358,7 +362,7 @@ def measure_slabs(lbm, p, phi, args, mlups_single, dist, n_slabs=4):
     return {"n_slabs": n_slabs, "mlups": round(mlups, 2), "ms_per_step": round(ms / args.steps, 5),
             "vs_whole_domain": round(mlups / mlups_single, 4),
             "launches_per_step": n_slabs + 2, "exchange_bytes_per_step": exch,
-            "slab_kernel_traffic": _traffic("slab_f32")}
+            "slab_kernel_traffic": _traffic("slab_f32", full_size=args.n == 4096)}
 
 
 def measure_lagged(lbm, p, phi, args, peak, mlups_sync, dist):
@@ -393,7 +397,7 @@ def measure_lagged(lbm, p, phi, args, peak, mlups_sync, dist):
     return {"mlups": round(mlups, 2), "ms_per_step": round(total / args.steps, 5),
             "vs_synchronous": round(mlups / mlups_sync, 4), "bytes_per_cell": bpc,
             "hbm_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
-            "traffic": _traffic("lag_f32"), "kernel": "k_strip_lag_tma<float> (interior strips' g and f rows by TMA tensor tiles)",
+            "traffic": _traffic("lag_f32", full_size=args.n == 4096), "kernel": "k_strip_lag_tma<float> (interior strips' g and f rows by TMA tensor tiles)",
             "max_abs_diff_vs_synchronous": diff, "steps_for_diff": args.steps + args.warmup}
 
 
@@ -490,6 +494,8 @@ def main():
     ap.add_argument("--no-lagged", action="store_true", help="skip the lagged-grad-p variant")
     ap.add_argument("--no-3d", action="store_true", help="skip the D3Q19 workload")
     ap.add_argument("--n3", type=int, default=256, help="side of the D3Q19 workload")
+    ap.add_argument("--batch-domains", type=int, default=1024,
+                    help="domains of the batched workload (the first n of its 1024; smaller for ncu captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -554,7 +560,7 @@ def main():
                        "l2": "no flush: populations 2.4 GB per time level > 129 MB L2"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
-                         "traffic": _traffic("f32"), "peak_kind": peak_kind,
+                         "traffic": _traffic("f32", full_size=args.n == 4096), "peak_kind": peak_kind,
                          "bytes_per_cell": BYTES_PER_CELL["f32"],
                          "kernel": ("k_strip_tma<float> (rows of interior strips by TMA tensor tiles)"
                                     if n % 8 == 0 else "k_step<float>"),
@@ -583,7 +589,8 @@ def main():
             ach2 = BYTES_PER_CELL[dtype] * cells / (statistics.mean(per2) * 1e-3) / 1e9
             forms[dtype] = {"mlups": round(m2, 2), "ms_per_step": round(tot / ksteps, 5),
                             "hbm_gbs": round(ach2, 1), "frac": round(ach2 / peak, 4),
-                            "bytes_per_cell": BYTES_PER_CELL[dtype], "traffic": _traffic(dtype)}
+                            "bytes_per_cell": BYTES_PER_CELL[dtype],
+                            "traffic": _traffic(dtype, full_size=args.n == 4096)}
             a64 = _alu("f64") if dtype == "f64" else None
             if a64 and "f64" in peaks:
                 # FP64 add, multiply and FMA each take one FP64 pipe slot
