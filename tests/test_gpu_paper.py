@@ -26,11 +26,20 @@ from paper_1507_03521_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-# (Pe, Cn, paper's sigma_LBM / sigma, droplet radius).  The paper's radii
-# range from 20 to 40 without saying which Table I used; R = 40 keeps the
+# (Pe, Cn, paper's sigma_LBM / sigma, droplet radius), the paper's values
+# from tests/golden/table1_surface_tension.json.  The paper's radii range
+# from 20 to 40 without saying which Table I used; R = 40 keeps the
 # interface width W = Cn below 0.2 R for Cn = 6 and 8.
-TABLE1 = [(50.0, 4.0, 0.992, 25.0), (125.0, 4.0, 0.992, 25.0), (200.0, 4.0, 0.992, 25.0),
-          (200.0, 6.0, 0.993, 40.0), (200.0, 8.0, 0.989, 40.0)]
+def _table1():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "table1_surface_tension.json")) as f:
+        g = json.load(f)
+    return [(c["Pe"], c["Cn"], c["sigma_lbm_over_1e-3"], 25.0 if c["Cn"] == 4.0 else 40.0)
+            for c in g["cases"]]
+
+
+TABLE1 = _table1()
 
 
 @pytest.fixture(scope="module")

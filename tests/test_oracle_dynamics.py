@@ -159,8 +159,9 @@ def test_flat_interface_profile(orc, Cn, Pe, tol):
 def test_laplace_law_table1(orc):
     """Sec. 4.2 / Table I: stationary droplet, 100 x 100, R = 25, Pe = 50,
     Cn = 4, sigma = 1e-3.  sigma_LBM = R dP with dP the jump of the total
-    pressure P; the paper reports 0.992e-3.  The pressure rings acoustically
-    after the start from p = 0, so dP is averaged over steps 8000-10000."""
+    pressure P; the paper reports 0.992e-3 (tests/golden/
+    table1_surface_tension.json).  The pressure rings acoustically after
+    the start from p = 0, so dP is averaged over steps 8000-10000."""
     p, phi = W.paper_droplet(R=25.0)
     o = orc.Oracle(p)
     o.init_phi(phi)
@@ -171,7 +172,12 @@ def test_laplace_law_table1(orc):
         vals.append(dP * Reff)
         o.step(500)
     ratio = np.mean(vals) / 1e-3
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "table1_surface_tension.json")) as f:
+        paper = [c for c in json.load(f)["cases"] if c["Pe"] == 50.0 and c["Cn"] == 4.0][0]
     assert abs(ratio - 1.0) < 0.015
+    assert abs(ratio - paper["sigma_lbm_over_1e-3"]) < 0.02
     assert abs(Reff - 25.0) < 0.2
 
 
