@@ -811,246 +811,260 @@ __device__ __forceinline__ void strip_body(const char *__restrict__ src, char *_
     T n_ux = 0, n_uy = 0, n_Fx = 0, n_Fy = 0, n_lm = 0, n_gx = 0, n_gy = 0;
     T c_f[9] = {}, n_f[9] = {};  // own f values (FCARRY): row y, row y+1
 
-    for (int y = yfirst; y < ye; ++y) {
-        if (tma) {
-            // g row y+3 and (once the segment needs it) f row y+1 have landed
-            if (__syncthreads_or(!wait_rows(y))) {  // rows y-1 are free; or a wait ran out
-                if (t == 0 && P.err) atomicOr(P.err, 1u);
-                // wait (bounded) for the loads still in flight into this
-                // CTA's shared memory, those of iterations y+1 .. y+DEPTH-1,
-                // so that none lands after the CTA has gone
-                for (int d = 1; d < DEPTH; ++d)
-                    if (y + d < ye) wait_rows(y + d);
-                return;
+    // The row loop runs as two copies (the outer loop is unrolled, so
+    // `warm` is a constant in each).  The warm-up copy (y < ys) computes
+    // only what the segment's collisions read: phi from row ys-3 on, mu
+    // from row ys-2 on, p from row ys-1 on (earlier rows of the rings are
+    // never read), and takes no barrier before a step it skips (the
+    // conditions hold for the whole CTA alike); every iteration still
+    // starts with the barrier at its top.  The main copy (the segment's
+    // own rows) runs every step.
+    const int ymid = ys < ye ? ys : ye;
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool warm = pass == 0;
+        for (int y = warm ? yfirst : ymid; y < (warm ? ymid : ye); ++y) {
+            if (tma) {
+                // g row y+3 and (once the segment needs it) f row y+1 have landed
+                if (__syncthreads_or(!wait_rows(y))) {  // rows y-1 are free; or a wait ran out
+                    if (t == 0 && P.err) atomicOr(P.err, 1u);
+                    // wait (bounded) for the loads still in flight into this
+                    // CTA's shared memory, those of iterations y+1 .. y+DEPTH-1,
+                    // so that none lands after the CTA has gone
+                    for (int d = 1; d < DEPTH; ++d)
+                        if (y + d < ye) wait_rows(y + d);
+                    return;
+                }
+            } else {
+                cp_async_wait<DEPTH - 1>();   // g row y+3, f row y+1 have landed (own chunks)
+                __syncthreads();              // ... everyone's; rows y-1 are free
             }
-        } else {
-            cp_async_wait<DEPTH - 1>();   // g row y+3, f row y+1 have landed (own chunks)
-            __syncthreads();              // ... everyone's; rows y-1 are free
-        }
-        issue_for(y + DEPTH, R.g[SM::NBG - 1], R.f[SM::NBF - 1]);
+            issue_for(y + DEPTH, R.g[SM::NBG - 1], R.f[SM::NBF - 1]);
+            const bool run_mu = !warm || y >= ys - 4, run_p = !warm || y >= ys - 2, run_col = !warm;
 
-        // 1. phi at row y+3, columns -3 .. SW+2
-        {
-            const char *b = at(R.g[3]);
-            T *ph = atT(R.ph[3]);
-            columns<SW, 3, 3>(t, [&](int c) {
-                if (!LBM_IDX_OK(P, c >= -3 && c < SW + 3 && c + HP >= 0 && c + HP < SR::LW, 3)) return;
-                T g[9];
-                SR::read_g(b, c + HP, g);
-                ph[c] = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
-            });
-        }
-        __syncthreads();
-
-        // 3. mu at row y+2, columns -2 .. SW+1 (Eq. 5)
-        {
-            const int r = y + 2;
-            T *mo = atT(R.mu[SM::MU0 + 2]);
-            const bool ghost = wall && (r < 0 || r >= ny);
-            if (!ghost) {
-                const T *pu = atT(R.ph[3]), *pc = atT(R.ph[2]), *pd = atT(R.ph[1]);
-                T *mlow = (wall && r == 0) ? atT(R.mu[SM::MU0 + 1]) : nullptr;  // row -1
-                columns<SW, 2, 1>(t, [&](int c) {
-                    if (!LBM_IDX_OK(P, c >= -2 && c < SW + 2, 4)) return;
-                    const T C = pc[c];
-                    // lap = (2/cs2) sum w_i (phi(x + c_i) - phi(x)), differences first
-                    const T ax = ((pc[c + 1] - C) + (pc[c - 1] - C)) + ((pu[c] - C) + (pd[c] - C));
-                    const T dg = ((pu[c + 1] - C) + (pu[c - 1] - C)) + ((pd[c - 1] - C) + (pd[c + 1] - C));
-                    const T lap = T(2.0 / 3.0) * ax + T(1.0 / 6.0) * dg;
-                    const T m = P.beta4 * (C - P.phiA) * (C - P.phiB) * (C - P.phibar) - P.kappa * lap;
-                    mo[c] = m;
-                    if (mlow) mlow[c] = m;  // ghost row -1 mirrors row 0
+            // 1. phi at row y+3, columns -3 .. SW+2
+            {
+                const char *b = at(R.g[3]);
+                T *ph = atT(R.ph[3]);
+                columns<SW, 3, 3>(t, [&](int c) {
+                    if (!LBM_IDX_OK(P, c >= -3 && c < SW + 3 && c + HP >= 0 && c + HP < SR::LW, 3)) return;
+                    T g[9];
+                    SR::read_g(b, c + HP, g);
+                    ph[c] = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
                 });
-            } else if (r == ny) {
-                const T *mm = atT(R.mu[SM::MU0 + 1]);  // mirror row ny-1 (already computed)
-                columns<SW, 2, 1>(t, [&](int c) { mo[c] = mm[c]; });
             }
-            // r < 0 at a wall: row -1 is written when row 0 is computed;
-            // rows below -1 and above ny are never read.
-        }
-        __syncthreads();
+            if (run_mu) __syncthreads();
 
-        // 4. p at row y+1, columns -1 .. SW (Eq. 32), from sum f and j of
-        //    that row and phi, mu around it; thread t also keeps u, F,
-        //    lap mu and grad phi of its own column t for the next
-        //    iteration's collision (Eq. 31), in registers.
-        {
-            const int r = y + 1;
-            T *po = atT(R.p[2]);
-            if (!wall || (r >= 0 && r < ny)) {
-                const T *pu = atT(R.ph[2]), *pc = atT(R.ph[1]), *pd = atT(R.ph[0]);
-                const T *mu_ = atT(R.mu[SM::MU0 + 2]), *mc = atT(R.mu[SM::MU0 + 1]),
-                        *md = atT(R.mu[SM::MU0]);
-                const char *fbr = at(R.f[SM::F1]);
-                auto point = [&](int c, bool keep) {
-                    if (!LBM_IDX_OK(P, c >= -1 && c < SW + 1 && c + HP >= 0 && c + HP < SR::LW, 3)) return;
-                    T f[9];
-                    SR::read_f(fbr, c + HP, f);
-                    const T sf = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-                    const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-                    const T jy = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
-                    const T phi = pc[c];
-                    const T pul = pu[c - 1], pur = pu[c + 1], pdl = pd[c - 1], pdr = pd[c + 1];
-                    const T gphx = T(1.0 / 3.0) * (pc[c + 1] - pc[c - 1]) +
-                                   T(1.0 / 12.0) * ((pur - pul) + (pdr - pdl));
-                    const T gphy = T(1.0 / 3.0) * (pu[c] - pd[c]) +
-                                   T(1.0 / 12.0) * ((pur + pul) - (pdl + pdr));
-                    const T M = mc[c];
-                    const T mul = mu_[c - 1], mur_ = mu_[c + 1], mdl = md[c - 1], mdr = md[c + 1];
-                    const T mcl = mc[c - 1], mcr = mc[c + 1], mcu = mu_[c], mcd = md[c];
-                    const T gmx = T(1.0 / 3.0) * (mcr - mcl) + T(1.0 / 12.0) * ((mur_ - mul) + (mdr - mdl));
-                    const T gmy = T(1.0 / 3.0) * (mcu - mcd) + T(1.0 / 12.0) * ((mur_ + mul) - (mdl + mdr));
-                    const T lm = T(2.0 / 3.0) * (((mcl - M) + (mcr - M)) + ((mcu - M) + (mcd - M))) +
-                                 T(1.0 / 6.0) * (((mur_ - M) + (mul - M)) + ((mdl - M) + (mdr - M)));
-                    const T rho = P.rhoB + (phi - P.phiB) * P.drho;
-                    const T Fx = -phi * gmx;
-                    const T Fy = -phi * gmy - (rho - P.rhoref) * P.grav;
-                    const T irc = T(3) * rcp_fast(rho);
-                    const T ux = (jx + c6 * Fx) * irc;
-                    const T uy = (jy + c6 * Fy) * irc;
-                    const T udr = (ux * gphx + uy * gphy) * P.drho;
-                    po[c] = sf + c6 * (udr - P.gl * rho * lm);
-                    if (keep) {
-                        n_ux = ux;
-                        n_uy = uy;
-                        n_Fx = Fx;
-                        n_Fy = Fy;
-                        n_lm = lm;
-                        n_gx = gphx;
-                        n_gy = gphy;
-                        if constexpr (SM::FCARRY) {
-#pragma unroll
-                            for (int i = 0; i < 9; ++i) n_f[i] = f[i];
-                        }
-                    }
-                };
-                if constexpr (strip_threads(SW) >= SW + 2) {
-                    // one pass: thread t takes column t - 1 (and collides it)
-                    if (t < SW + 2) point(t - 1, t >= 1 && t <= SW);
-                } else {
-                    if (t < SW) point(t, true);
-                    // halo columns -1 and SW: two lanes of the last warp
-                    if (t >= SW - 32 && t < SW - 30) point(t == SW - 32 ? -1 : SW, false);
+            // 3. mu at row y+2, columns -2 .. SW+1 (Eq. 5)
+            if (run_mu) {
+                const int r = y + 2;
+                T *mo = atT(R.mu[SM::MU0 + 2]);
+                const bool ghost = wall && (r < 0 || r >= ny);
+                if (!ghost) {
+                    const T *pu = atT(R.ph[3]), *pc = atT(R.ph[2]), *pd = atT(R.ph[1]);
+                    T *mlow = (wall && r == 0) ? atT(R.mu[SM::MU0 + 1]) : nullptr;  // row -1
+                    columns<SW, 2, 1>(t, [&](int c) {
+                        if (!LBM_IDX_OK(P, c >= -2 && c < SW + 2, 4)) return;
+                        const T C = pc[c];
+                        // lap = (2/cs2) sum w_i (phi(x + c_i) - phi(x)), differences first
+                        const T ax = ((pc[c + 1] - C) + (pc[c - 1] - C)) + ((pu[c] - C) + (pd[c] - C));
+                        const T dg = ((pu[c + 1] - C) + (pu[c - 1] - C)) + ((pd[c - 1] - C) + (pd[c + 1] - C));
+                        const T lap = T(2.0 / 3.0) * ax + T(1.0 / 6.0) * dg;
+                        const T m = P.beta4 * (C - P.phiA) * (C - P.phiB) * (C - P.phibar) - P.kappa * lap;
+                        mo[c] = m;
+                        if (mlow) mlow[c] = m;  // ghost row -1 mirrors row 0
+                    });
+                } else if (r == ny) {
+                    const T *mm = atT(R.mu[SM::MU0 + 1]);  // mirror row ny-1 (already computed)
+                    columns<SW, 2, 1>(t, [&](int c) { mo[c] = mm[c]; });
                 }
-            } else if (r == ny) {
-                // ghost row above the top wall: linear extrapolation of p
-                const T *p1 = atT(R.p[1]), *p2 = atT(R.p[0]);  // rows ny-1, ny-2
-                columns<SW, 1, 0>(t, [&](int c) { po[c] = T(2) * p1[c] - p2[c]; });
+                // r < 0 at a wall: row -1 is written when row 0 is computed;
+                // rows below -1 and above ny are never read.
             }
-        }
-        __syncthreads();
+            if (run_p) __syncthreads();
 
-        // 5. collide row y and push (Eqs. 22-29, Gamma_i = 1 + s_i): the
-        //    column whose u, F, lap mu, grad phi this thread kept in step 4
-        if (y >= ys) {
-            constexpr int shift = strip_threads(SW) >= SW + 2 ? 1 : 0;
-            const int c = t - shift;
-            const int gx = x0 + c;
-            if (c >= 0 && c < SW && gx < nx) {
-                const T *pc = atT(R.p[1]), *pu = atT(R.p[2]), *pd = atT(R.p[0]);
-                const bool lowghost = wall && y == 0;
-                const T pdm = lowghost ? T(2) * pc[c - 1] - pu[c - 1] : pd[c - 1];
-                const T pd0 = lowghost ? T(2) * pc[c] - pu[c] : pd[c];
-                const T pdp = lowghost ? T(2) * pc[c + 1] - pu[c + 1] : pd[c + 1];
-                const T gpx = T(1.0 / 3.0) * (pc[c + 1] - pc[c - 1]) +
-                              T(1.0 / 12.0) * ((pu[c + 1] - pu[c - 1]) + (pdp - pdm));
-                const T gpy = T(1.0 / 3.0) * (pu[c] - pd0) +
-                              T(1.0 / 12.0) * ((pu[c + 1] + pu[c - 1]) - (pdm + pdp));
-                const T phi = atT(R.ph[0])[c];
-                const T mu = atT(R.mu[SM::MU0])[c];
-                const T pv = pc[c];
-                const T rho = P.rhoB + (phi - P.phiB) * P.drho;
-                T f[9], g[9];
-                if constexpr (SM::FCARRY) {
+            // 4. p at row y+1, columns -1 .. SW (Eq. 32), from sum f and j of
+            //    that row and phi, mu around it; thread t also keeps u, F,
+            //    lap mu and grad phi of its own column t for the next
+            //    iteration's collision (Eq. 31), in registers.
+            if (run_p) {
+                const int r = y + 1;
+                T *po = atT(R.p[2]);
+                if (!wall || (r >= 0 && r < ny)) {
+                    const T *pu = atT(R.ph[2]), *pc = atT(R.ph[1]), *pd = atT(R.ph[0]);
+                    const T *mu_ = atT(R.mu[SM::MU0 + 2]), *mc = atT(R.mu[SM::MU0 + 1]),
+                            *md = atT(R.mu[SM::MU0]);
+                    const char *fbr = at(R.f[SM::F1]);
+                    auto point = [&](int c, bool keep) {
+                        if (!LBM_IDX_OK(P, c >= -1 && c < SW + 1 && c + HP >= 0 && c + HP < SR::LW, 3)) return;
+                        T f[9];
+                        SR::read_f(fbr, c + HP, f);
+                        const T sf = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+                        const T jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+                        const T jy = (f[2] - f[4]) + (f[5] - f[8]) + (f[6] - f[7]);
+                        const T phi = pc[c];
+                        const T pul = pu[c - 1], pur = pu[c + 1], pdl = pd[c - 1], pdr = pd[c + 1];
+                        const T gphx = T(1.0 / 3.0) * (pc[c + 1] - pc[c - 1]) +
+                                       T(1.0 / 12.0) * ((pur - pul) + (pdr - pdl));
+                        const T gphy = T(1.0 / 3.0) * (pu[c] - pd[c]) +
+                                       T(1.0 / 12.0) * ((pur + pul) - (pdl + pdr));
+                        const T M = mc[c];
+                        const T mul = mu_[c - 1], mur_ = mu_[c + 1], mdl = md[c - 1], mdr = md[c + 1];
+                        const T mcl = mc[c - 1], mcr = mc[c + 1], mcu = mu_[c], mcd = md[c];
+                        const T gmx = T(1.0 / 3.0) * (mcr - mcl) + T(1.0 / 12.0) * ((mur_ - mul) + (mdr - mdl));
+                        const T gmy = T(1.0 / 3.0) * (mcu - mcd) + T(1.0 / 12.0) * ((mur_ + mul) - (mdl + mdr));
+                        const T lm = T(2.0 / 3.0) * (((mcl - M) + (mcr - M)) + ((mcu - M) + (mcd - M))) +
+                                     T(1.0 / 6.0) * (((mur_ - M) + (mul - M)) + ((mdl - M) + (mdr - M)));
+                        const T rho = P.rhoB + (phi - P.phiB) * P.drho;
+                        const T Fx = -phi * gmx;
+                        const T Fy = -phi * gmy - (rho - P.rhoref) * P.grav;
+                        const T irc = T(3) * rcp_fast(rho);
+                        const T ux = (jx + c6 * Fx) * irc;
+                        const T uy = (jy + c6 * Fy) * irc;
+                        const T udr = (ux * gphx + uy * gphy) * P.drho;
+                        po[c] = sf + c6 * (udr - P.gl * rho * lm);
+                        if (keep) {
+                            n_ux = ux;
+                            n_uy = uy;
+                            n_Fx = Fx;
+                            n_Fy = Fy;
+                            n_lm = lm;
+                            n_gx = gphx;
+                            n_gy = gphy;
+                            if constexpr (SM::FCARRY) {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) f[i] = c_f[i];
-                } else {
-                    SR::read_f(at(R.f[0]), c + HP, f);
-                }
-                SR::read_g(at(R.g[0]), c + HP, g);
-                T fv[9], gv[9];
-                collide(P, CellState<T>{phi, mu, pv, rho, c_ux, c_uy, c_Fx, c_Fy, c_lm, c_gx, c_gy,
-                                        gpx, gpy},
-                        f, g, fv, gv);
-                // pushes that neither wrap nor meet a wall (a slab's pushes
-                // across its edges land in its ghost rows)
-                const bool y_inner = (y > 0 && y < ny - 1) || (SLAB && !wall);
-                const int yl = SLAB ? y - P.y0 : y;  // row within the level
-                // deviation storage: the references of the destination
-                // cells, p and alpha mu of rows y-1 .. y+1 (cut)
-                float rP[9], rA[9];
-                if constexpr (SM::DEV) {
-                    const T *mrow[3] = {atT(R.mu[SM::MU0 - 1]), atT(R.mu[SM::MU0]),
-                                        atT(R.mu[SM::MU0 + 1])};
-                    const T *prow[3] = {pd, pc, pu};
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        const int cx = D2Q9::cx(i), cy = D2Q9::cy(i);
-                        rP[i] = ST::ref_cut(prow[cy + 1][c + cx]);
-                        rA[i] = ST::ref_cut(P.alpha * mrow[cy + 1][c + cx]);
-                    }
-                }
-                // every push lands inside the level: the farthest are
-                // kb - nx - 1 and kb + nx + 1 on the fast path
-                if (x_inner && y_inner &&
-                    LBM_IDX_OK(P, (yl - 1) * nx + gx - 1 >= 0 && (yl + 1) * nx + gx + 1 < lvl_rows * nx, 2)) {
-                    if constexpr (SM::DEV)
-                        SR::store_fast(dst, NS, nx, yl * nx + gx, fv, gv, phi, rP, rA, pv,
-                                       P.alpha * mu);
-                    else
-                        SR::store_fast(dst, NS, nx, yl * nx + gx, fv, gv, phi);
-                } else {
-                    int sl[9];
-                    long long kk[9];
-                    const long long k = (long long)yl * nx + gx;
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) {
-                        const int cx = D2Q9::cx(i), cy = D2Q9::cy(i);
-                        const int yd = y + cy;
-                        if (wall && (yd < 0 || yd >= ny)) {
-                            const T w = T(D2Q9::w(i));
-                            const T cuw = T(cx) * (yd < 0 ? P.uwb : P.uwt);
-                            fv[i] -= T(2) * w * rho * cuw;
-                            gv[i] -= T(6) * w * phi * cuw;
-                            sl[i] = D2Q9::opp(i);
-                            kk[i] = k;
-                            if constexpr (SM::DEV) {  // bounced back: this cell's references
-                                rP[i] = rP[0];
-                                rA[i] = rA[0];
+                                for (int i = 0; i < 9; ++i) n_f[i] = f[i];
                             }
-                        } else {
-                            int xd = gx + cx;
-                            xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
-                            const int yy = SLAB ? yd - P.y0
-                                                : (yd < 0 ? yd + ny : (yd >= ny ? yd - ny : yd));
-                            sl[i] = i;
-                            kk[i] = (long long)yy * nx + xd;
                         }
+                    };
+                    if constexpr (strip_threads(SW) >= SW + 2) {
+                        // one pass: thread t takes column t - 1 (and collides it)
+                        if (t < SW + 2) point(t - 1, t >= 1 && t <= SW);
+                    } else {
+                        if (t < SW) point(t, true);
+                        // halo columns -1 and SW: two lanes of the last warp
+                        if (t >= SW - 32 && t < SW - 30) point(t == SW - 32 ? -1 : SW, false);
                     }
-                    bool in = true;
-#pragma unroll
-                    for (int i = 0; i < 9; ++i)
-                        in = in && kk[i] >= 0 && kk[i] < (long long)lvl_rows * nx && sl[i] >= 0 && sl[i] < 9;
-                    if (!LBM_IDX_OK(P, in, 2)) {
-                    } else if constexpr (SM::DEV)
-                        ST::store(dst, P.NS, sl, kk, fv, gv, phi, rP, rA, pv, P.alpha * mu);
-                    else
-                        ST::store(dst, P.NS, sl, kk, fv, gv, phi);
+                } else if (r == ny) {
+                    // ghost row above the top wall: linear extrapolation of p
+                    const T *p1 = atT(R.p[1]), *p2 = atT(R.p[0]);  // rows ny-1, ny-2
+                    columns<SW, 1, 0>(t, [&](int c) { po[c] = T(2) * p1[c] - p2[c]; });
                 }
             }
-        }
-        c_ux = n_ux;
-        c_uy = n_uy;
-        c_Fx = n_Fx;
-        c_Fy = n_Fy;
-        c_lm = n_lm;
-        c_gx = n_gx;
-        c_gy = n_gy;
-        if constexpr (SM::FCARRY) {
+            if (run_col) __syncthreads();
+
+            // 5. collide row y and push (Eqs. 22-29, Gamma_i = 1 + s_i): the
+            //    column whose u, F, lap mu, grad phi this thread kept in step 4
+            if (run_col) {
+                constexpr int shift = strip_threads(SW) >= SW + 2 ? 1 : 0;
+                const int c = t - shift;
+                const int gx = x0 + c;
+                if (c >= 0 && c < SW && gx < nx) {
+                    const T *pc = atT(R.p[1]), *pu = atT(R.p[2]), *pd = atT(R.p[0]);
+                    const bool lowghost = wall && y == 0;
+                    const T pdm = lowghost ? T(2) * pc[c - 1] - pu[c - 1] : pd[c - 1];
+                    const T pd0 = lowghost ? T(2) * pc[c] - pu[c] : pd[c];
+                    const T pdp = lowghost ? T(2) * pc[c + 1] - pu[c + 1] : pd[c + 1];
+                    const T gpx = T(1.0 / 3.0) * (pc[c + 1] - pc[c - 1]) +
+                                  T(1.0 / 12.0) * ((pu[c + 1] - pu[c - 1]) + (pdp - pdm));
+                    const T gpy = T(1.0 / 3.0) * (pu[c] - pd0) +
+                                  T(1.0 / 12.0) * ((pu[c + 1] + pu[c - 1]) - (pdm + pdp));
+                    const T phi = atT(R.ph[0])[c];
+                    const T mu = atT(R.mu[SM::MU0])[c];
+                    const T pv = pc[c];
+                    const T rho = P.rhoB + (phi - P.phiB) * P.drho;
+                    T f[9], g[9];
+                    if constexpr (SM::FCARRY) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) c_f[i] = n_f[i];
+                        for (int i = 0; i < 9; ++i) f[i] = c_f[i];
+                    } else {
+                        SR::read_f(at(R.f[0]), c + HP, f);
+                    }
+                    SR::read_g(at(R.g[0]), c + HP, g);
+                    T fv[9], gv[9];
+                    collide(P, CellState<T>{phi, mu, pv, rho, c_ux, c_uy, c_Fx, c_Fy, c_lm, c_gx, c_gy,
+                                            gpx, gpy},
+                            f, g, fv, gv);
+                    // pushes that neither wrap nor meet a wall (a slab's pushes
+                    // across its edges land in its ghost rows)
+                    const bool y_inner = (y > 0 && y < ny - 1) || (SLAB && !wall);
+                    const int yl = SLAB ? y - P.y0 : y;  // row within the level
+                    // deviation storage: the references of the destination
+                    // cells, p and alpha mu of rows y-1 .. y+1 (cut)
+                    float rP[9], rA[9];
+                    if constexpr (SM::DEV) {
+                        const T *mrow[3] = {atT(R.mu[SM::MU0 - 1]), atT(R.mu[SM::MU0]),
+                                            atT(R.mu[SM::MU0 + 1])};
+                        const T *prow[3] = {pd, pc, pu};
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) {
+                            const int cx = D2Q9::cx(i), cy = D2Q9::cy(i);
+                            rP[i] = ST::ref_cut(prow[cy + 1][c + cx]);
+                            rA[i] = ST::ref_cut(P.alpha * mrow[cy + 1][c + cx]);
+                        }
+                    }
+                    // every push lands inside the level: the farthest are
+                    // kb - nx - 1 and kb + nx + 1 on the fast path
+                    if (x_inner && y_inner &&
+                        LBM_IDX_OK(P, (yl - 1) * nx + gx - 1 >= 0 && (yl + 1) * nx + gx + 1 < lvl_rows * nx, 2)) {
+                        if constexpr (SM::DEV)
+                            SR::store_fast(dst, NS, nx, yl * nx + gx, fv, gv, phi, rP, rA, pv,
+                                           P.alpha * mu);
+                        else
+                            SR::store_fast(dst, NS, nx, yl * nx + gx, fv, gv, phi);
+                    } else {
+                        int sl[9];
+                        long long kk[9];
+                        const long long k = (long long)yl * nx + gx;
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) {
+                            const int cx = D2Q9::cx(i), cy = D2Q9::cy(i);
+                            const int yd = y + cy;
+                            if (wall && (yd < 0 || yd >= ny)) {
+                                const T w = T(D2Q9::w(i));
+                                const T cuw = T(cx) * (yd < 0 ? P.uwb : P.uwt);
+                                fv[i] -= T(2) * w * rho * cuw;
+                                gv[i] -= T(6) * w * phi * cuw;
+                                sl[i] = D2Q9::opp(i);
+                                kk[i] = k;
+                                if constexpr (SM::DEV) {  // bounced back: this cell's references
+                                    rP[i] = rP[0];
+                                    rA[i] = rA[0];
+                                }
+                            } else {
+                                int xd = gx + cx;
+                                xd = xd < 0 ? xd + nx : (xd >= nx ? xd - nx : xd);
+                                const int yy = SLAB ? yd - P.y0
+                                                    : (yd < 0 ? yd + ny : (yd >= ny ? yd - ny : yd));
+                                sl[i] = i;
+                                kk[i] = (long long)yy * nx + xd;
+                            }
+                        }
+                        bool in = true;
+#pragma unroll
+                        for (int i = 0; i < 9; ++i)
+                            in = in && kk[i] >= 0 && kk[i] < (long long)lvl_rows * nx && sl[i] >= 0 && sl[i] < 9;
+                        if (!LBM_IDX_OK(P, in, 2)) {
+                        } else if constexpr (SM::DEV)
+                            ST::store(dst, P.NS, sl, kk, fv, gv, phi, rP, rA, pv, P.alpha * mu);
+                        else
+                            ST::store(dst, P.NS, sl, kk, fv, gv, phi);
+                    }
+                }
+            }
+            c_ux = n_ux;
+            c_uy = n_uy;
+            c_Fx = n_Fx;
+            c_Fy = n_Fy;
+            c_lm = n_lm;
+            c_gx = n_gx;
+            c_gy = n_gy;
+            if constexpr (SM::FCARRY) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) c_f[i] = n_f[i];
+            }
+            R.advance();
         }
-        R.advance();
     }
     cp_async_wait<0>();
 }
