@@ -335,16 +335,21 @@ struct AdjCell {
 
 // grad p transposed (extrapolated ghosts) gives the full adjoint of p; then
 // p, u, F backwards (Eqs. 31-32) and the f terms through sum f and j.
-// FP32: 4 CTAs per SM (64 registers) instead of 3 at 80 registers measured
-// 7% faster over the whole backward pass at 512^2.
+// FP32: 3 CTAs per SM (80 registers).  With every load of a cell before
+// its first store, 4 CTAs per SM (64 registers) spill 128 bytes and the
+// whole backward pass at 512^2 measured 2.4% slower.
 template <class T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_adj_p(T *__restrict__ lam, const AdjP<T> P, AdjW<T> W) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_adj_p(T *__restrict__ lam, const AdjP<T> P, AdjW<T> W) {
     const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
     const long long N = (long long)P.k.nx * P.k.ny, NS = P.k.NS;
     const KP<T> &K = P.k;
     const T *gbx = W[B_GPX], *gby = W[B_GPY];
     ADJ_LOOP(k, N) {
         const int y = row_of(k, B.nx), x = (int)(k - (long long)y * B.nx);
+        // Every load of the cell comes before its first store: the work
+        // arrays and lambda are views of allocations the compiler cannot
+        // tell apart, so a load placed after a store would wait for it,
+        // one L2 round trip after another.
         const T bp = W[B_P][k] + tgather(B, x, y, true, [&](long long c, int i, T coef) {
                          return coef * T(3.0 * D2Q9::w(i)) *
                                 (T(D2Q9::cx(i)) * gbx[c] + T(D2Q9::cy(i)) * gby[c]);
@@ -352,22 +357,30 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_adj_p(T *__rest
         const T rho = W[A_RHO][k], phi = W[A_PHI][k], lm = W[A_LMU][k];
         const T ux = W[A_UX][k], uy = W[A_UY][k];
         const T gphx = W[A_GPHX][k], gphy = W[A_GPHY][k];
+        const T gmux = W[A_GMUX][k], gmuy = W[A_GMUY][k];
+        const T bux0 = W[B_UX][k], buy0 = W[B_UY][k], bgrx = W[B_GRX][k], bgry = W[B_GRY][k];
+        const T blm0 = W[B_LMU][k], brho0 = W[B_RHO][k], bgl0 = W[B_GL][k];
+        const T bFx0 = W[B_FX][k], bFy0 = W[B_FY][k], bphi0 = W[B_PHI][k];
+        T l[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) l[i] = lam[i * NS + k];
         // p = sum f + (drho u.grad phi - gamma lambda rho lap mu) / 6
-        const T bux = W[B_UX][k] + K.drho / T(6) * gphx * bp;
-        const T buy = W[B_UY][k] + K.drho / T(6) * gphy * bp;
-        const T bgphx = K.drho / T(6) * ux * bp + K.drho * W[B_GRX][k];
-        const T bgphy = K.drho / T(6) * uy * bp + K.drho * W[B_GRY][k];
-        const T blm = W[B_LMU][k] - K.gl / T(6) * rho * bp;
-        T brho = W[B_RHO][k] - K.gl / T(6) * lm * bp;
-        W[B_GL][k] += -rho * lm / T(6) * bp;
+        const T bux = bux0 + K.drho / T(6) * gphx * bp;
+        const T buy = buy0 + K.drho / T(6) * gphy * bp;
+        const T bgphx = K.drho / T(6) * ux * bp + K.drho * bgrx;
+        const T bgphy = K.drho / T(6) * uy * bp + K.drho * bgry;
+        const T blm = blm0 - K.gl / T(6) * rho * bp;
+        T brho = brho0 - K.gl / T(6) * lm * bp;
+        const T bgl = bgl0 + -rho * lm / T(6) * bp;
         // u = (j + F/6) 3 / rho
         const T jx = T(3) / rho * bux, jy = T(3) / rho * buy;
-        const T bFx = W[B_FX][k] + bux / (T(2) * rho);
-        const T bFy = W[B_FY][k] + buy / (T(2) * rho);
+        const T bFx = bFx0 + bux / (T(2) * rho);
+        const T bFy = bFy0 + buy / (T(2) * rho);
         brho += -(ux * bux + uy * buy) / rho;
         // F = -phi grad mu + (0, -(rho - rho_ref) g)
         brho += -K.grav * bFy;
-        W[B_PHI][k] += -(W[A_GMUX][k] * bFx + W[A_GMUY][k] * bFy);
+        W[B_GL][k] = bgl;
+        W[B_PHI][k] = bphi0 + -(gmux * bFx + gmuy * bFy);
         W[B_GMUX][k] = -phi * bFx;
         W[B_GMUY][k] = -phi * bFy;
         W[B_GPHX][k] = bgphx;
@@ -377,7 +390,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_adj_p(T *__rest
         // sum f and j feed every f_i
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-            lam[i * NS + k] += bp + T(D2Q9::cx(i)) * jx + T(D2Q9::cy(i)) * jy;
+            lam[i * NS + k] = l[i] + (bp + T(D2Q9::cx(i)) * jx + T(D2Q9::cy(i)) * jy);
     }
 }
 
@@ -418,11 +431,13 @@ __device__ __forceinline__ void adj_theta_partials(double dM, double dS, double 
 // folds the partial sums into the running totals, in the same fixed order
 // as k_adj_accumulate.  64-column tiles, two cells per thread: a 512^2
 // grid has 512 tiles, all resident at once (with 32-column tiles its 1024
-// tiles took two rounds of the 608 CTAs the partial sums allow).
+// tiles took two rounds of the 608 CTAs the partial sums allow).  FP32:
+// held to 4 CTAs per SM (64 registers, no spill) so that those 512 tiles
+// stay resident at once.
 constexpr int kMpTX = 64, kMpTY = 8;
 
 template <class T>
-__global__ void __launch_bounds__(256) k_adj_muphi(T *__restrict__ lam, const AdjP<T> P, AdjW<T> W,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_adj_muphi(T *__restrict__ lam, const AdjP<T> P, AdjW<T> W,
                                                    double *__restrict__ part, double *__restrict__ acc,
                                                    unsigned *__restrict__ ticket) {
     constexpr int HX = kMpTX + 2, HY = kMpTY + 2;
@@ -494,8 +509,12 @@ __global__ void __launch_bounds__(256) k_adj_muphi(T *__restrict__ lam, const Ad
             }
             const T bm = smu[sy0][sx0];
             const T bphi = W[B_PHI][k] + K.drho * W[B_RHO][k] + psi2 * bm + t + K.kappa * T(10.0 / 3.0) * bm;
+            // the nine loads before the nine stores (see k_adj_p)
+            T l[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) lam[(9 + i) * NS + k] += bphi;
+            for (int i = 0; i < 9; ++i) l[i] = lam[(9 + i) * NS + k];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) lam[(9 + i) * NS + k] = l[i] + bphi;
         }
         __syncthreads();
     }
