@@ -441,7 +441,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_adj_muphi(T *__
                                                    double *__restrict__ part, double *__restrict__ acc,
                                                    unsigned *__restrict__ ticket) {
     constexpr int HX = kMpTX + 2, HY = kMpTY + 2;
-    __shared__ T smu[HY][HX];
+    // mu_bar and the grad phi adjoint on the tile and its ring
+    __shared__ T smu[HY][HX], sgx[HY][HX], sgy[HY][HX];
     __shared__ bool last;
     const Nb<T> B{P.k.nx, P.k.ny, P.k.wall};
     const KP<T> &K = P.k;
@@ -469,6 +470,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_adj_muphi(T *__
             });
             const T bmu = W[B_MU][k] + t - T(10.0 / 3.0) * bl[k];
             smu[hy][hx] = bmu;
+            sgx[hy][hx] = gpx[k];
+            sgy[hy][hx] = gpy[k];
             if (hx >= 1 && hx <= kMpTX && hy >= 1 && hy <= kMpTY && xv < nx && yv < ny) {
                 dM += a1 * (double)W[B_ALPHA][k] + gm * (double)W[B_GL][k];
                 dS += (double)(bmu * W[A_MU1][k]);
@@ -485,11 +488,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_adj_muphi(T *__
             const T ph = W[A_PHI][k];
             const T a = ph - K.phiA, b = ph - K.phiB, m = ph - K.phibar;
             const T psi2 = K.beta4 * (a * b + a * m + b * m);
-            // tgather's terms in its order; mu_bar of a source centre from
-            // shared memory (the centre's tile position), its grad phi
-            // adjoint from global memory
+            // tgather's terms in its order; mu_bar and the grad phi adjoint
+            // of a source centre from shared memory (the centre's tile
+            // position, which the first phase filled from cell c)
             auto term = [&](long long c, int hx, int hy, int i, T coef) {
-                return coef * (T(3.0 * D2Q9::w(i)) * (T(D2Q9::cx(i)) * gpx[c] + T(D2Q9::cy(i)) * gpy[c]) -
+                (void)c;
+                return coef * (T(3.0 * D2Q9::w(i)) * (T(D2Q9::cx(i)) * sgx[hy][hx] + T(D2Q9::cy(i)) * sgy[hy][hx]) -
                                K.kappa * T(6.0 * D2Q9::w(i)) * smu[hy][hx]);
             };
             T t = T(0);
